@@ -1,0 +1,199 @@
+/*
+ * gadi.h -- C ABI of the GB300 GADI / GADI-IR solver library (libgadi.so).
+ *
+ * Problem (arXiv 2501.04229, §1.2 and §2.1): solve A x = b, A real n x n,
+ * nonsingular, split as A = M + N. GADI iterates eq. (gadi):
+ *     (aI + M) x^{k+1/2} = (aI - N) x^k + b
+ *     (aI + N) x^{k+1}   = (N - (1-w) aI) x^k + (2-w) a x^{k+1/2}
+ * for a > 0, w in [0, 2) (Thm 1). GADI-IR (Algorithm 1) runs the same
+ * iteration as a refinement loop in three precisions:
+ *     r = b - A x                      precision u_f
+ *     solve H z = r,   H = aI + M      precision u_r
+ *     solve S y = (2-w) a z, S = aI+N  precision u_r
+ *     x = x + y                        precision u
+ * The default splitting is HSS (§4.1): M = (A + A^T)/2, N = (A - A^T)/2.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns gadi_status. Nothing aborts, exits or prints.
+ *   - Arguments are checked before anything is modified; on
+ *     GADI_ERR_INVALID_ARG nothing has changed.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ *   - Device pointers are CUDA device (or managed) addresses on the device
+ *     that was current when the handle was created; host pointers are
+ *     ordinary (pageable or pinned) host memory. Where both are accepted the
+ *     library tells them apart with cudaPointerGetAttributes.
+ *   - All device work is ordered on the stream given to gadi_create.
+ *   - gadi_last_error(h) returns a NUL-terminated description of the last
+ *     failure on h (owned by h, valid until the next call on h).
+ */
+#ifndef GADI_H
+#define GADI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gadi_solver gadi_solver;   /* opaque, owned by the library */
+
+typedef enum {
+    GADI_OK = 0,
+    GADI_ERR_INVALID_ARG = 1,    /* bad argument; nothing was modified */
+    GADI_ERR_OUT_OF_MEMORY = 2,  /* a device allocation failed */
+    GADI_ERR_CUDA = 3,           /* a CUDA runtime call failed; see gadi_last_error */
+    GADI_ERR_RANGE = 4,          /* a value cannot be represented in the inner precision
+                                    even after power-of-two scaling */
+    GADI_ERR_NOT_CONVERGED = 5,  /* max_outer reached; x holds the last iterate */
+    GADI_ERR_DIVERGED = 6,       /* NaN/Inf, inner breakdown, or residual growth > 1e3x */
+    GADI_ERR_TIMEOUT = 7,        /* a bounded device-side wait expired */
+    GADI_ERR_NO_MODEL = 8,       /* no parameter predictor of the requested kind */
+    GADI_ERR_UNSUPPORTED = 9     /* valid request this build does not implement */
+} gadi_status;
+
+typedef enum { GADI_SPLIT_HSS = 0, GADI_SPLIT_USER = 1 } gadi_splitting;
+
+typedef enum { GADI_F64 = 0, GADI_F32 = 1, GADI_F16 = 2, GADI_BF16 = 3 } gadi_precision;
+
+typedef enum {
+    GADI_STOP_ETA = 0,   /* stop when eta_inf = ||b-Ax||_inf/(||A||_inf ||x||_inf + ||b||_inf) <= tol */
+    GADI_STOP_RES = 1    /* stop when RES = ||b-Ax||_2/||b-Ax0||_2 <= tol (§4.1's RES) */
+} gadi_stop;
+
+typedef enum {
+    GADI_KERNEL_AUTO = 0,     /* stencil kernels when a stencil descriptor was given, else sparse */
+    GADI_KERNEL_SPARSE = 1,   /* general sparse (ELL layout built from the CSR) */
+    GADI_KERNEL_STENCIL = 2   /* matrix-free 5/7-point stencil; needs a stencil descriptor */
+} gadi_kernel;
+
+/* Sparse matrix in CSR form, int32 indices, FP64 values. Column indices of a
+ * row must be ascending and the pattern structurally symmetric (a_ij stored
+ * iff a_ji stored), which the HSS splitting needs. Caller-owned; gadi_create
+ * copies it, so the caller may free it as soon as gadi_create returns.
+ * on_device: 0 = the three arrays are host pointers, 1 = device pointers. */
+typedef struct {
+    int64_t n, nnz;
+    const int32_t *row_ptr;   /* n+1 entries, row_ptr[0] = 0, row_ptr[n] = nnz */
+    const int32_t *col_idx;   /* nnz entries */
+    const double *val;        /* nnz entries */
+    int32_t on_device;
+} gadi_csr;
+
+/* Optional structure of A for the matrix-free kernels: the h^2-scaled
+ * centred-difference convection-diffusion operator of §4.1 on an N^dim grid
+ * of interior nodes (x fastest), h = 1/(N+1), convection c = beta*h/2:
+ * row i has diagonal sum_f k_f over its 2*dim faces, -k_f - c towards the
+ * lower neighbour along each axis and -k_f + c towards the upper one.
+ * k_faces: NULL for k = 1, else (dim = 3 only) three host FP64 arrays:
+ *   k_faces[0] shape (N, N, N+1) index (iz, iy, fx)   face fx between nodes fx-1, fx
+ *   k_faces[1] shape (N, N+1, N) index (iz, fy, ix)
+ *   k_faces[2] shape (N+1, N, N) index (fz, iy, ix)
+ * gadi_create checks that the CSR matrix equals this operator entry by entry
+ * (relative difference <= 1e-12) and rejects the descriptor otherwise. */
+typedef struct {
+    int32_t dim, N;
+    double beta;
+    const double *const *k_faces;
+} gadi_stencil;
+
+typedef struct {
+    int32_t outer_iters;        /* completed refinement steps */
+    int32_t status;             /* the gadi_status of the solve */
+    int64_t inner_iters_H;      /* total CG iterations on H */
+    int64_t inner_iters_S;      /* total CGNR iterations on S */
+    int64_t spmv_count;         /* operator applications in the solve (A, H, S, S^T) */
+    double eta_inf;             /* backward error of the returned x */
+    double res_rel;             /* RES of the returned x */
+    double t_solve_s;           /* device time of the solve (CUDA events) */
+    int32_t scale_exp_M;        /* FP16 scale exponent of H (H stored as 2^-s H) */
+    int32_t scale_exp_N;        /* FP16 scale exponent of S */
+    int32_t kernel;             /* gadi_kernel actually used */
+    int32_t grid_blocks;        /* persistent-kernel launch shape used */
+    int32_t block_threads;
+    int32_t reserved;
+} gadi_info;
+
+/* Create a solver for A (copied to the device). split: GADI_SPLIT_HSS, or
+ * GADI_SPLIT_USER with M_user on A's exact pattern (same row_ptr/col_idx,
+ * same on_device flag) and N = A - M; M must be symmetric for the CG on
+ * H = aI + M to apply. structure: optional stencil descriptor (see above).
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * Errors: INVALID_ARG (n < 1, bad pattern, pattern not symmetric, unsorted
+ * columns, non-finite values, stencil mismatch), OUT_OF_MEMORY, CUDA. */
+gadi_status gadi_create(const gadi_csr *A, gadi_splitting split, const gadi_csr *M_user,
+                        const gadi_stencil *structure, void *cuda_stream, gadi_solver **out);
+
+/* Parameters of eq. (gadi) and the precision triple of Algorithm 1.
+ * alpha > 0 and omega in [0, 2) (Thm 1). Supported: u = u_f = GADI_F64 and
+ * u_r in {GADI_F16, GADI_F64}; other valid triples return UNSUPPORTED.
+ * u_r = GADI_F16 means FP16 storage of the inner matrix values and vectors
+ * with FP32 arithmetic; A, r and z are scaled by powers of two so FP16 stays
+ * in range, and (2 - omega) alpha is applied in the FP64 update.
+ * u_r = GADI_F64 with the default inner tolerance is plain FP64 GADI. */
+gadi_status gadi_set_params(gadi_solver *h, double alpha, double omega,
+                            gadi_precision u_r, gadi_precision u, gadi_precision u_f);
+
+/* Inner relative tolerance eps (0 < eps < 1): each inner solve stops when
+ * ||rhs - K v||_2 <= eps ||rhs||_2, or after max_inner iterations (>= 1).
+ * max_outer (>= 0) caps the refinement steps. Defaults: eps 1e-2 (FP16
+ * inner) / 1e-10 (FP64 inner), max_inner 200, max_outer 100000. */
+gadi_status gadi_set_inner(gadi_solver *h, double eps_inner, int32_t max_inner, int32_t max_outer);
+
+/* Stopping criterion kind for gadi_solve's tol (default GADI_STOP_ETA). */
+gadi_status gadi_set_stop(gadi_solver *h, gadi_stop kind);
+
+/* Kernel family (default GADI_KERNEL_AUTO). STENCIL without a descriptor
+ * returns INVALID_ARG. */
+gadi_status gadi_set_kernel(gadi_solver *h, gadi_kernel kind);
+
+/* Launch shape of the persistent solve kernel: grid_blocks (0 = automatic,
+ * else 1 .. the co-resident maximum) and block_threads (0 = automatic, else
+ * 128, 256, 512 or 1024). One block runs the solve with block-local barriers
+ * only. */
+gadi_status gadi_set_launch(gadi_solver *h, int32_t grid_blocks, int32_t block_threads);
+
+/* Upper bound, in milliseconds, of every device-side grid-barrier wait
+ * (default 2000). An expired wait ends the solve with GADI_ERR_TIMEOUT and
+ * leaves the handle usable. */
+gadi_status gadi_set_wait_limit(gadi_solver *h, double milliseconds);
+
+/* Solve A x = b. b (n FP64) and x (n FP64; in: x0, out: the result) are
+ * both host or both device pointers. Host buffers are copied to and from
+ * library-owned device memory inside the call. Returns after the result is
+ * in x (the stream is synchronised). tol > 0 applies to the criterion set
+ * by gadi_set_stop. Returns OK, NOT_CONVERGED, DIVERGED (x holds the last
+ * iterate), TIMEOUT, INVALID_ARG (tol <= 0, non-finite b, mixed pointer
+ * kinds) or CUDA. info may be NULL. */
+gadi_status gadi_solve(gadi_solver *h, const double *b, double *x, double tol, gadi_info *info);
+
+/* One operator application with the solver's current kernel and parameters,
+ * y = K x, for kernel-level tests and bandwidth measurement. which:
+ *   0: K = A      (FP64 x, y)
+ *   1: K = H' = 2^-sM (aI + M)  in the inner precision (x, y FP16 or FP64)
+ *   2: K = S' = 2^-sN (aI + N)
+ *   3: K = S'^T
+ * x, y are device pointers of n elements of the inner precision (FP64 for
+ * which = 0). Asynchronous on the handle's stream. */
+gadi_status gadi_apply(gadi_solver *h, int32_t which, const void *x, void *y);
+
+/* Scale exponents (sM, sN) that the inner operators use for the current
+ * alpha and inner precision. */
+gadi_status gadi_get_scales(gadi_solver *h, int32_t *sM, int32_t *sN);
+
+/* Predict (alpha, omega) from problem features (§3.3). features[0] = log n,
+ * features[1] = log beta. kind: 0 MLP, 1 GPR, 2 grid search. Returns
+ * NO_MODEL when no predictor of that kind has been loaded. */
+gadi_status gadi_predict_params(gadi_solver *h, const double *features, int32_t nfeat,
+                                int32_t kind, double *alpha, double *omega);
+
+/* Release all device memory of h. NULL is accepted. */
+void gadi_destroy(gadi_solver *h);
+
+const char *gadi_status_str(gadi_status s);
+const char *gadi_last_error(const gadi_solver *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GADI_H */

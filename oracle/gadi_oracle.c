@@ -1,0 +1,755 @@
+/*
+ * gadi_oracle.c -- plain, slow, obviously correct CPU implementation of GADI
+ * and GADI-IR (arXiv 2501.04229).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the library path may call, link or
+ * load this file; only the tests, the smoke check and the bench's CPU
+ * baseline do. It shares no code with the CUDA path.
+ *
+ * What it implements, and where the paper defines it:
+ *   or_hss_split      M = (A+A^T)/2, N = (A-A^T)/2                 (§4.1, HSS splitting)
+ *   or_spmv_shift     y = (sigma I + V) x                          (H = aI+M, S = aI+N, §1.4)
+ *   or_cg             CG on the SPD system (sigma I + M) v = rhs    (inner solver, §2.2: "backward stable")
+ *   or_cgnr           CG on the normal equations of (sigma I + N)   (inner solver, §2.2)
+ *   or_gadi           the two-half-step GADI iteration             (eq. (gadi), §2.1)
+ *   or_gadi_ir        three-precision GADI-IR                      (Algorithm 1, §2.1)
+ *   or_backward_error eta_inf = ||b-Ax||_inf/(||A||_inf ||x||_inf + ||b||_inf)  (Thm 3 measure)
+ *
+ * Readings of the paper that this file takes (the paper is silent there):
+ *   - inner solvers: CG for H = aI+M (SPD), CGNR for S = aI+N (N skew);
+ *   - inner stopping: ||rhs - K v||_2 <= eps * ||rhs - K v0||_2 (relative to the
+ *     inner initial residual), with an iteration cap;
+ *   - residual sign r = b - Ax; start x0 given by the caller (zero in the
+ *     paper's experiments);
+ *   - FP16 inner precision ("half"): FP16 storage of matrix values and inner
+ *     vectors, FP32 arithmetic; the matrix, the residual and the first
+ *     correction are scaled by powers of two so that FP16 stays in range; the
+ *     shift alpha is applied in FP32 and (2-omega)*alpha is folded into the
+ *     FP64 update scalar. The "naive" half mode instead rounds alpha into the
+ *     FP16 diagonal and scales nothing, for the paper's unscaled behaviour.
+ *
+ * Determinism: dot products are summed in fixed blocks of OR_BLK elements and
+ * the block sums are added in order, so results do not depend on the number
+ * of OpenMP threads. Compile with -ffp-contract=off.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_INVALID 1
+#define OR_OOM 2
+#define OR_NOT_CONVERGED 5
+#define OR_DIVERGED 6
+
+#define OR_BLK 4096
+/* loops over fewer elements than this run on one thread */
+#define OR_PAR_MIN 32768
+
+enum { OR_PREC_DOUBLE = 0, OR_PREC_SINGLE = 1, OR_PREC_HALF = 2, OR_PREC_HALF_NAIVE = 3 };
+enum { OR_STOP_ETA = 0, OR_STOP_RES = 1 };
+
+typedef struct {
+    double alpha, omega;     /* GADI parameters, alpha > 0, omega in [0, 2) (Thm 1) */
+    double tol;              /* outer stopping tolerance on eta_inf or RES */
+    double eps_inner;        /* inner relative tolerance */
+    int32_t max_inner, max_outer;
+    int32_t stop_kind;       /* OR_STOP_ETA or OR_STOP_RES */
+    int32_t inner_prec;      /* OR_PREC_* (GADI-IR only) */
+} or_params;
+
+typedef struct {
+    int32_t status, outer_iters;
+    int64_t inner_iters_H, inner_iters_S, spmv_count;
+    double eta_inf, res_rel, res0;
+    int32_t scale_exp_M, scale_exp_N;   /* FP16 matrix scale exponents (half mode) */
+} or_info;
+
+void or_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* FP64 vector helpers                                                 */
+/* ------------------------------------------------------------------ */
+
+static double dot64(int64_t n, const double *a, const double *b)
+{
+    int64_t nb = (n + OR_BLK - 1) / OR_BLK;
+    double *part = (double *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(double));
+    #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t k = 0; k < nb; ++k) {
+        int64_t lo = k * OR_BLK, hi = lo + OR_BLK < n ? lo + OR_BLK : n;
+        double s = 0.0;
+        for (int64_t i = lo; i < hi; ++i) s += a[i] * b[i];
+        part[k] = s;
+    }
+    double s = 0.0;
+    for (int64_t k = 0; k < nb; ++k) s += part[k];
+    free(part);
+    return s;
+}
+
+static double norm_inf64(int64_t n, const double *a)
+{
+    double m = 0.0;
+    #pragma omp parallel for reduction(max : m) schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) {
+        double v = fabs(a[i]);
+        if (v > m || v != v) m = (v != v) ? INFINITY : v;
+    }
+    return m;
+}
+
+/* y = (sigma I + V) x, V in CSR */
+void or_spmv_shift(int64_t n, const int32_t *rp, const int32_t *ci, const double *v,
+                   double sigma, const double *x, double *y)
+{
+    #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = sigma * x[i];
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * x[ci[k]];
+        y[i] = s;
+    }
+}
+
+/* r = b - A x */
+void or_residual(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+                 const double *b, const double *x, double *r)
+{
+    #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s += a[k] * x[ci[k]];
+        r[i] = b[i] - s;
+    }
+}
+
+double or_matrix_norm_inf(int64_t n, const int32_t *rp, const double *a)
+{
+    double m = 0.0;
+    #pragma omp parallel for reduction(max : m) schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s += fabs(a[k]);
+        if (s > m) m = s;
+    }
+    return m;
+}
+
+/* Normwise backward error in the infinity norm (the measure of Thm 3 with the
+ * b term added): ||b - Ax||_inf / (||A||_inf ||x||_inf + ||b||_inf). */
+double or_backward_error(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+                         const double *b, const double *x)
+{
+    double *r = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    or_residual(n, rp, ci, a, b, x, r);
+    double num = norm_inf64(n, r);
+    double den = or_matrix_norm_inf(n, rp, a) * norm_inf64(n, x) + norm_inf64(n, b);
+    free(r);
+    if (den == 0.0) return num == 0.0 ? 0.0 : INFINITY;
+    return num / den;
+}
+
+/* ------------------------------------------------------------------ */
+/* HSS splitting (§4.1): M = (A + A^T)/2, N = (A - A^T)/2 on A's pattern */
+/* ------------------------------------------------------------------ */
+
+static int32_t find_in_row(const int32_t *rp, const int32_t *ci, int64_t row, int64_t col)
+{
+    int32_t lo = rp[row], hi = rp[row + 1] - 1;
+    while (lo <= hi) {
+        int32_t mid = lo + (hi - lo) / 2;
+        if (ci[mid] == col) return mid;
+        if (ci[mid] < col) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* Returns OR_OK, or OR_INVALID when A's pattern is not symmetric or a row's
+ * columns are not sorted ascending (then M and N are left undefined). */
+int or_hss_split(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+                 double *m, double *nv)
+{
+    int bad = 0;
+    #pragma omp parallel for schedule(static) reduction(| : bad) if (n > OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            if (k > rp[i] && ci[k] <= ci[k - 1]) { bad = 1; continue; }
+            int64_t j = ci[k];
+            if (j < 0 || j >= n) { bad = 1; continue; }
+            int32_t kt = find_in_row(rp, ci, j, i);
+            if (kt < 0) { bad = 1; continue; }
+            m[k] = 0.5 * (a[k] + a[kt]);
+            nv[k] = 0.5 * (a[k] - a[kt]);
+        }
+    }
+    return bad ? OR_INVALID : OR_OK;
+}
+
+/* Explicit transpose of a CSR matrix (counting sort by column). */
+static int transpose_csr(int64_t n, const int32_t *rp, const int32_t *ci, const double *v,
+                         int32_t **rpt, int32_t **cit, double **vt)
+{
+    int64_t nnz = rp[n];
+    *rpt = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    *cit = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    *vt = (double *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+    int32_t *fill = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!*rpt || !*cit || !*vt || !fill) { free(fill); return OR_OOM; }
+    for (int64_t k = 0; k < nnz; ++k) (*rpt)[ci[k] + 1]++;
+    for (int64_t i = 0; i < n; ++i) (*rpt)[i + 1] += (*rpt)[i];
+    for (int64_t i = 0; i < n; ++i) fill[i] = (*rpt)[i];
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            int32_t pos = fill[ci[k]]++;
+            (*cit)[pos] = (int32_t)i;
+            (*vt)[pos] = v[k];
+        }
+    free(fill);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* FP64 inner solvers                                                  */
+/* ------------------------------------------------------------------ */
+
+/* CG for (sigma I + M) v = rhs, M symmetric, starting from v (in/out).
+ * Stops when ||rhs - K v||_2 <= eps ||rhs - K v0||_2 or after maxit SpMVs.
+ * Returns the number of SpMVs inside the loop; -1 on breakdown (p.q <= 0 or
+ * non-finite). */
+int64_t or_cg(int64_t n, const int32_t *rp, const int32_t *ci, const double *m, double sigma,
+              const double *rhs, double *v, double eps, int32_t maxit)
+{
+    size_t sz = (size_t)(n > 0 ? n : 1) * sizeof(double);
+    double *r = (double *)malloc(sz), *p = (double *)malloc(sz), *q = (double *)malloc(sz);
+    or_spmv_shift(n, rp, ci, m, sigma, v, q);
+    #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) { r[i] = rhs[i] - q[i]; p[i] = r[i]; }
+    double rr = dot64(n, r, r), rr0 = rr;
+    int64_t it = 0;
+    if (rr0 > 0.0) {
+        while (it < maxit) {
+            or_spmv_shift(n, rp, ci, m, sigma, p, q);
+            ++it;
+            double pq = dot64(n, p, q);
+            if (!(pq > 0.0) || !isfinite(pq)) { it = -1; break; }
+            double a = rr / pq;
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) { v[i] += a * p[i]; r[i] -= a * q[i]; }
+            double rrn = dot64(n, r, r);
+            if (!isfinite(rrn)) { it = -1; break; }
+            if (rrn <= eps * eps * rr0) break;
+            double beta = rrn / rr;
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+            rr = rrn;
+        }
+    }
+    free(r); free(p); free(q);
+    return it;
+}
+
+/* CGNR for S v = rhs with S = sigma I + V: CG on S^T S v = S^T rhs, where
+ * S^T = sigma I + V^T (Vt is V's explicit transpose). Same stopping rule as
+ * or_cg, on the residual of S v = rhs. Counts one per SpMV with S or S^T. */
+int64_t or_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const double *vv,
+                const int32_t *rpt, const int32_t *cit, const double *vt, double sigma,
+                const double *rhs, double *v, double eps, int32_t maxit)
+{
+    size_t sz = (size_t)(n > 0 ? n : 1) * sizeof(double);
+    double *r = (double *)malloc(sz), *s = (double *)malloc(sz);
+    double *p = (double *)malloc(sz), *q = (double *)malloc(sz);
+    or_spmv_shift(n, rp, ci, vv, sigma, v, q);
+    #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) r[i] = rhs[i] - q[i];
+    double rr0 = dot64(n, r, r);
+    int64_t it = 0;
+    if (rr0 > 0.0) {
+        or_spmv_shift(n, rpt, cit, vt, sigma, r, s);
+        ++it;
+        memcpy(p, s, sz);
+        double g = dot64(n, s, s);
+        while (it < maxit) {
+            or_spmv_shift(n, rp, ci, vv, sigma, p, q);
+            ++it;
+            double qq = dot64(n, q, q);
+            if (!(qq > 0.0) || !isfinite(qq)) { it = -1; break; }
+            double a = g / qq;
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) { v[i] += a * p[i]; r[i] -= a * q[i]; }
+            double rr = dot64(n, r, r);
+            if (!isfinite(rr)) { it = -1; break; }
+            if (rr <= eps * eps * rr0) break;
+            or_spmv_shift(n, rpt, cit, vt, sigma, r, s);
+            ++it;
+            double gn = dot64(n, s, s);
+            double beta = gn / g;
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) p[i] = s[i] + beta * p[i];
+            g = gn;
+        }
+    }
+    free(r); free(s); free(p); free(q);
+    return it;
+}
+
+/* ------------------------------------------------------------------ */
+/* Low-precision inner solvers: FP32 arithmetic, storage rounded to the */
+/* inner precision (FP32 itself, or FP16 emulated with _Float16).       */
+/* Every stored value is the result of rnd(); every sum runs in float.  */
+/* ------------------------------------------------------------------ */
+
+static inline float rnd_store(float x, int half)
+{
+    return half ? (float)(_Float16)x : x;
+}
+
+static float dot32(int64_t n, const float *a, const float *b)
+{
+    int64_t nb = (n + OR_BLK - 1) / OR_BLK;
+    float *part = (float *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(float));
+    #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t k = 0; k < nb; ++k) {
+        int64_t lo = k * OR_BLK, hi = lo + OR_BLK < n ? lo + OR_BLK : n;
+        float s = 0.0f;
+        for (int64_t i = lo; i < hi; ++i) s += a[i] * b[i];
+        part[k] = s;
+    }
+    float s = 0.0f;
+    for (int64_t k = 0; k < nb; ++k) s += part[k];
+    free(part);
+    return s;
+}
+
+static float norm_inf32(int64_t n, const float *a)
+{
+    float m = 0.0f;
+    #pragma omp parallel for reduction(max : m) schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) {
+        float v = fabsf(a[i]);
+        if (v > m || v != v) m = (v != v) ? INFINITY : v;
+    }
+    return m;
+}
+
+/* y = rnd(sigma x + V x), V values already rounded to storage precision */
+static void spmv32(int64_t n, const int32_t *rp, const int32_t *ci, const float *v,
+                   float sigma, const float *x, float *y, int half)
+{
+    #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) {
+        float s = sigma * x[i];
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * x[ci[k]];
+        y[i] = rnd_store(s, half);
+    }
+}
+
+/* CG on (sigma I + M) z = rhs from z = 0, low precision. */
+static int64_t lp_cg(int64_t n, const int32_t *rp, const int32_t *ci, const float *m, float sigma,
+                     const float *rhs, float *z, double eps, int32_t maxit, int half)
+{
+    size_t sz = (size_t)(n > 0 ? n : 1) * sizeof(float);
+    float *r = (float *)malloc(sz), *p = (float *)malloc(sz), *q = (float *)malloc(sz);
+    memcpy(r, rhs, sz); memcpy(p, rhs, sz);
+    memset(z, 0, sz);
+    float rr = dot32(n, r, r), rr0 = rr;
+    float eps2 = (float)(eps * eps);
+    int64_t it = 0;
+    if (rr0 > 0.0f) {
+        while (it < maxit) {
+            spmv32(n, rp, ci, m, sigma, p, q, half);
+            ++it;
+            float pq = dot32(n, p, q);
+            if (!(pq > 0.0f) || !isfinite(pq)) { it = -1; break; }
+            float a = rr / pq;
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) {
+                z[i] = rnd_store(z[i] + a * p[i], half);
+                r[i] = rnd_store(r[i] - a * q[i], half);
+            }
+            float rrn = dot32(n, r, r);
+            if (!isfinite(rrn)) { it = -1; break; }
+            if (rrn <= eps2 * rr0) break;
+            float beta = rrn / rr;
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) p[i] = rnd_store(r[i] + beta * p[i], half);
+            rr = rrn;
+        }
+    }
+    free(r); free(p); free(q);
+    return it;
+}
+
+/* CGNR on (sigma I + N) y = rhs from y = 0, low precision. */
+static int64_t lp_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const float *nv,
+                       const int32_t *rpt, const int32_t *cit, const float *nvt, float sigma,
+                       const float *rhs, float *y, double eps, int32_t maxit, int half)
+{
+    size_t sz = (size_t)(n > 0 ? n : 1) * sizeof(float);
+    float *r = (float *)malloc(sz), *s = (float *)malloc(sz);
+    float *p = (float *)malloc(sz), *q = (float *)malloc(sz);
+    memcpy(r, rhs, sz);
+    memset(y, 0, sz);
+    float rr0 = dot32(n, r, r);
+    float eps2 = (float)(eps * eps);
+    int64_t it = 0;
+    if (rr0 > 0.0f) {
+        spmv32(n, rpt, cit, nvt, sigma, r, s, half);
+        ++it;
+        memcpy(p, s, sz);
+        float g = dot32(n, s, s);
+        while (it < maxit) {
+            spmv32(n, rp, ci, nv, sigma, p, q, half);
+            ++it;
+            float qq = dot32(n, q, q);
+            if (!(qq > 0.0f) || !isfinite(qq)) { it = -1; break; }
+            float a = g / qq;
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) {
+                y[i] = rnd_store(y[i] + a * p[i], half);
+                r[i] = rnd_store(r[i] - a * q[i], half);
+            }
+            float rr = dot32(n, r, r);
+            if (!isfinite(rr)) { it = -1; break; }
+            if (rr <= eps2 * rr0) break;
+            spmv32(n, rpt, cit, nvt, sigma, r, s, half);
+            ++it;
+            float gn = dot32(n, s, s);
+            float beta = gn / g;
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) p[i] = rnd_store(s[i] + beta * p[i], half);
+            g = gn;
+        }
+    }
+    free(r); free(s); free(p); free(q);
+    return it;
+}
+
+/* floor(log2 |v|) for finite v > 0 */
+static int ilog2_floor(double v)
+{
+    int e;
+    frexp(v, &e);
+    return e - 1;
+}
+
+/* FP16 range scale of an operator sigma I + V: the exponent s for which
+ * (|sigma| + max row sum |V|) * 2^-s lies in (1, 2]. Scaling by a power of
+ * two is exact, so this only keeps FP16 values in range: with the inner
+ * right-hand side scaled to infinity-norm [1, 2), a product K p (and, in
+ * CGNR, K K^T r) stays within a small multiple of the vector's own size. */
+static int half_scale_exponent(int64_t n, const int32_t *rp, const double *v, double sigma)
+{
+    double nrm = or_matrix_norm_inf(n, rp, v) + fabs(sigma);
+    if (!(nrm > 0.0) || !isfinite(nrm)) return 0;
+    int e;
+    double m = frexp(nrm, &e);       /* nrm = m 2^e, m in [0.5, 1) */
+    int c = (m == 0.5) ? e - 1 : e;  /* ceil(log2 nrm) */
+    return c - 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Outer iterations                                                    */
+/* ------------------------------------------------------------------ */
+
+static int check_params(const or_params *P)
+{
+    if (!(P->alpha > 0.0) || !isfinite(P->alpha)) return OR_INVALID;
+    if (!(P->omega >= 0.0 && P->omega < 2.0)) return OR_INVALID;
+    if (!(P->tol >= 0.0) || !(P->eps_inner > 0.0)) return OR_INVALID;
+    if (P->max_inner < 1 || P->max_outer < 0) return OR_INVALID;
+    return OR_OK;
+}
+
+typedef struct {
+    double anorm, bnorm, r0;
+    double best;
+} stop_state;
+
+/* Evaluate the stopping test on r = b - Ax (Alg. 1 loop condition, read as
+ * RES or eta_inf). Returns 1 to stop (converged), 0 to continue, -1 diverged. */
+static int outer_test(int64_t n, const double *r, const double *x, const or_params *P,
+                      stop_state *st, or_info *info, double *eta_hist, int k)
+{
+    double rn2 = sqrt(dot64(n, r, r));
+    double rinf = norm_inf64(n, r);
+    double den = st->anorm * norm_inf64(n, x) + st->bnorm;
+    double eta = den > 0.0 ? rinf / den : (rinf == 0.0 ? 0.0 : INFINITY);
+    if (k == 0) st->r0 = rn2;
+    double res = st->r0 > 0.0 ? rn2 / st->r0 : 0.0;
+    info->eta_inf = eta;
+    info->res_rel = res;
+    info->res0 = st->r0;
+    if (eta_hist) eta_hist[k] = eta;
+    if (!isfinite(rn2) || !isfinite(eta)) return -1;
+    if (k == 0 || rn2 < st->best) st->best = rn2;
+    double crit = P->stop_kind == OR_STOP_RES ? res : eta;
+    if (crit <= P->tol) return 1;
+    if (rn2 > 1e3 * st->best) return -1;
+    return 0;
+}
+
+/* Plain GADI, the two-half-step form of eq. (gadi), all in FP64:
+ *   (aI + M) x^{k+1/2} = (aI - N) x^k + b
+ *   (aI + N) x^{k+1}   = (N - (1-w) aI) x^k + (2-w) a x^{k+1/2}
+ * Each half step is solved by CG / CGNR started from x^k.
+ * x: in = x0, out = last iterate. eta_hist, itH, itS: optional per-iteration
+ * records of length max_outer + 1 (eta) and max_outer (inner counts). */
+int or_gadi(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+            const double *b, double *x, const or_params *P, or_info *info,
+            double *eta_hist, int32_t *itH, int32_t *itS)
+{
+    memset(info, 0, sizeof(*info));
+    if (check_params(P) != OR_OK) { info->status = OR_INVALID; return OR_INVALID; }
+    int64_t nnz = rp[n];
+    size_t szv = (size_t)(n > 0 ? n : 1) * sizeof(double);
+    size_t szm = (size_t)(nnz > 0 ? nnz : 1) * sizeof(double);
+    double *m = (double *)malloc(szm), *nv = (double *)malloc(szm);
+    if (or_hss_split(n, rp, ci, a, m, nv) != OR_OK) {
+        free(m); free(nv); info->status = OR_INVALID; return OR_INVALID;
+    }
+    int32_t *rpt, *cit; double *nvt;
+    transpose_csr(n, rp, ci, nv, &rpt, &cit, &nvt);
+    double *r = (double *)malloc(szv), *t = (double *)malloc(szv);
+    double *rhs = (double *)malloc(szv), *xh = (double *)malloc(szv), *xn = (double *)malloc(szv);
+    const double al = P->alpha, om = P->omega;
+    stop_state st = { or_matrix_norm_inf(n, rp, a), norm_inf64(n, b), 0.0, 0.0 };
+    int status = OR_NOT_CONVERGED;
+    int k = 0;
+    for (;;) {
+        or_residual(n, rp, ci, a, b, x, r);
+        info->spmv_count++;
+        int s = outer_test(n, r, x, P, &st, info, eta_hist, k);
+        if (s == 1) { status = OR_OK; break; }
+        if (s == -1) { status = OR_DIVERGED; break; }
+        if (k >= P->max_outer) break;
+        /* first half step: rhs = (aI - N) x + b, solve (aI + M) xh = rhs from x */
+        or_spmv_shift(n, rp, ci, nv, -al, x, t);     /* t = -a x + N x */
+        #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+        for (int64_t i = 0; i < n; ++i) { rhs[i] = b[i] - t[i]; xh[i] = x[i]; }
+        int64_t ih = or_cg(n, rp, ci, m, al, rhs, xh, P->eps_inner, P->max_inner);
+        if (ih < 0) { status = OR_DIVERGED; break; }
+        /* second half step: rhs = (N - (1-w) a I) x + (2-w) a xh, solve (aI + N) xn = rhs from x */
+        or_spmv_shift(n, rp, ci, nv, -(1.0 - om) * al, x, t);
+        #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+        for (int64_t i = 0; i < n; ++i) { rhs[i] = t[i] + (2.0 - om) * al * xh[i]; xn[i] = x[i]; }
+        int64_t is = or_cgnr(n, rp, ci, nv, rpt, cit, nvt, al, rhs, xn, P->eps_inner, P->max_inner);
+        if (is < 0) { status = OR_DIVERGED; break; }
+        memcpy(x, xn, szv);
+        info->inner_iters_H += ih;
+        info->inner_iters_S += is;
+        info->spmv_count += ih + is + 4;  /* + 2 rhs products + 2 initial inner residuals */
+        if (itH) itH[k] = (int32_t)ih;
+        if (itS) itS[k] = (int32_t)is;
+        ++k;
+    }
+    info->outer_iters = k;
+    info->status = status;
+    free(m); free(nv); free(rpt); free(cit); free(nvt);
+    free(r); free(t); free(rhs); free(xh); free(xn);
+    return status;
+}
+
+/* Three-precision GADI-IR, Algorithm 1:
+ *   step 1  r = b - A x                              (u_f = FP64)
+ *   step 2  solve H z = r,            H = aI + M     (u_r = inner_prec)
+ *   step 3  solve S y = (2-w) a z,    S = aI + N     (u_r)
+ *   step 4  x = x + y                                (u = FP64)
+ * until the stopping test holds. In the low-precision modes the residual is
+ * rounded to the inner precision (r^ = fl_r(s^), §2.2) after scaling by
+ * 2^-e, e = floor(log2 ||r||_inf); z is rescaled by 2^-ez before step 3; the
+ * scales and (2-w) a are applied to y in FP64 in step 4. */
+int or_gadi_ir(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+               const double *b, double *x, const or_params *P, or_info *info,
+               double *eta_hist, int32_t *itH, int32_t *itS)
+{
+    memset(info, 0, sizeof(*info));
+    if (check_params(P) != OR_OK || P->inner_prec < 0 || P->inner_prec > 3) {
+        info->status = OR_INVALID; return OR_INVALID;
+    }
+    int64_t nnz = rp[n];
+    size_t szv = (size_t)(n > 0 ? n : 1) * sizeof(double);
+    size_t szm = (size_t)(nnz > 0 ? nnz : 1) * sizeof(double);
+    double *m = (double *)malloc(szm), *nv = (double *)malloc(szm);
+    if (or_hss_split(n, rp, ci, a, m, nv) != OR_OK) {
+        free(m); free(nv); info->status = OR_INVALID; return OR_INVALID;
+    }
+    int32_t *rpt, *cit; double *nvt;
+    transpose_csr(n, rp, ci, nv, &rpt, &cit, &nvt);
+    const double al = P->alpha, om = P->omega, pfac = (2.0 - om) * al;
+    const int prec = P->inner_prec;
+    const int half = (prec == OR_PREC_HALF || prec == OR_PREC_HALF_NAIVE);
+    const int naive = (prec == OR_PREC_HALF_NAIVE);
+
+    double *r = (double *)malloc(szv), *z = (double *)malloc(szv), *y = (double *)malloc(szv);
+    /* low-precision copies */
+    size_t szvf = (size_t)(n > 0 ? n : 1) * sizeof(float);
+    size_t szmf = (size_t)(nnz > 0 ? nnz : 1) * sizeof(float);
+    float *mf = NULL, *nf = NULL, *nft = NULL, *rf = NULL, *zf = NULL, *yf = NULL;
+    float sigH = 0.0f, sigS = 0.0f;
+    int sM = 0, sN = 0;
+    if (prec != OR_PREC_DOUBLE) {
+        mf = (float *)malloc(szmf); nf = (float *)malloc(szmf); nft = (float *)malloc(szmf);
+        rf = (float *)malloc(szvf); zf = (float *)malloc(szvf); yf = (float *)malloc(szvf);
+        if (naive) {
+            /* alpha rounded into the stored diagonal, no scaling */
+            for (int64_t i = 0; i < n; ++i)
+                for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+                    double dm = m[k] + (ci[k] == i ? al : 0.0);
+                    double dn = nv[k] + (ci[k] == i ? al : 0.0);
+                    mf[k] = (float)(_Float16)dm;
+                    nf[k] = (float)(_Float16)dn;
+                }
+            for (int64_t i = 0; i < n; ++i)
+                for (int32_t k = rpt[i]; k < rpt[i + 1]; ++k) {
+                    double dn = nvt[k] + (cit[k] == i ? al : 0.0);
+                    nft[k] = (float)(_Float16)dn;
+                }
+            sigH = 0.0f; sigS = 0.0f;
+        } else {
+            if (half) {
+                sM = half_scale_exponent(n, rp, m, al);
+                sN = half_scale_exponent(n, rp, nv, al);
+            }
+            for (int64_t k = 0; k < nnz; ++k) {
+                mf[k] = half ? (float)(_Float16)ldexp(m[k], -sM) : (float)m[k];
+                nf[k] = half ? (float)(_Float16)ldexp(nv[k], -sN) : (float)nv[k];
+                nft[k] = half ? (float)(_Float16)ldexp(nvt[k], -sN) : (float)nvt[k];
+            }
+            sigH = (float)ldexp(al, -sM);
+            sigS = (float)ldexp(al, -sN);
+        }
+    }
+    info->scale_exp_M = sM;
+    info->scale_exp_N = sN;
+
+    stop_state st = { or_matrix_norm_inf(n, rp, a), norm_inf64(n, b), 0.0, 0.0 };
+    int status = OR_NOT_CONVERGED;
+    int k = 0;
+    for (;;) {
+        /* step 1: residual in u_f = FP64 */
+        or_residual(n, rp, ci, a, b, x, r);
+        info->spmv_count++;
+        int s = outer_test(n, r, x, P, &st, info, eta_hist, k);
+        if (s == 1) { status = OR_OK; break; }
+        if (s == -1) { status = OR_DIVERGED; break; }
+        if (k >= P->max_outer) break;
+        int64_t ih, is;
+        double upd;    /* y_true = upd * y_stored */
+        if (prec == OR_PREC_DOUBLE) {
+            /* steps 2-3 in FP64 */
+            memset(z, 0, szv);
+            ih = or_cg(n, rp, ci, m, al, r, z, P->eps_inner, P->max_inner);
+            if (ih < 0) { status = OR_DIVERGED; break; }
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) z[i] *= pfac;
+            memset(y, 0, szv);
+            is = or_cgnr(n, rp, ci, nv, rpt, cit, nvt, al, z, y, P->eps_inner, P->max_inner);
+            if (is < 0) { status = OR_DIVERGED; break; }
+            upd = 1.0;
+            /* step 4: x = x + y */
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) x[i] += y[i];
+        } else {
+            int e = 0, ez = 0;
+            if (!naive) {
+                double rinf = norm_inf64(n, r);
+                if (rinf > 0.0) e = ilog2_floor(rinf);
+            }
+            /* r^ = fl_r(r 2^-e) */
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) {
+                double v = ldexp(r[i], -e);
+                rf[i] = half ? (float)(_Float16)v : (float)v;
+            }
+            ih = lp_cg(n, rp, ci, mf, sigH, rf, zf, P->eps_inner, P->max_inner, half);
+            if (ih < 0) { status = OR_DIVERGED; break; }
+            if (naive) {
+                /* (2-w) a z formed in the inner precision */
+                float pf = (float)pfac;
+                #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+                for (int64_t i = 0; i < n; ++i) zf[i] = rnd_store(pf * zf[i], half);
+                upd = 1.0;
+            } else {
+                float zinf = norm_inf32(n, zf);
+                if (zinf > 0.0f && isfinite(zinf)) ez = ilog2_floor((double)zinf);
+                #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+                for (int64_t i = 0; i < n; ++i) zf[i] = rnd_store(ldexpf(zf[i], -ez), half);
+                upd = ldexp(pfac, e - sM + ez - sN);
+            }
+            is = lp_cgnr(n, rp, ci, nf, rpt, cit, nft, sigS, zf, yf, P->eps_inner, P->max_inner, half);
+            if (is < 0) { status = OR_DIVERGED; break; }
+            /* step 4 in u = FP64 */
+            #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) x[i] += upd * (double)yf[i];
+        }
+        info->inner_iters_H += ih;
+        info->inner_iters_S += is;
+        info->spmv_count += ih + is;
+        if (itH) itH[k] = (int32_t)ih;
+        if (itS) itS[k] = (int32_t)is;
+        ++k;
+    }
+    info->outer_iters = k;
+    info->status = status;
+    free(m); free(nv); free(rpt); free(cit); free(nvt);
+    free(r); free(z); free(y);
+    free(mf); free(nf); free(nft); free(rf); free(zf); free(yf);
+    return status;
+}
+
+/* FP64 -> FP16 conversion (round to nearest even, direct from double), as
+ * raw bits; used by the tests to pin the emulation against IEEE 754. */
+void or_to_half_bits(int64_t n, const double *in, uint16_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        _Float16 h = (_Float16)in[i];
+        memcpy(&out[i], &h, sizeof(uint16_t));
+    }
+}
+
+/* Single inner solves exposed for unit tests. */
+int64_t or_cg_solve(int64_t n, const int32_t *rp, const int32_t *ci, const double *m, double sigma,
+                    const double *rhs, double *v, double eps, int32_t maxit)
+{
+    return or_cg(n, rp, ci, m, sigma, rhs, v, eps, maxit);
+}
+
+int64_t or_cgnr_solve(int64_t n, const int32_t *rp, const int32_t *ci, const double *nv, double sigma,
+                      const double *rhs, double *v, double eps, int32_t maxit)
+{
+    int32_t *rpt, *cit; double *nvt;
+    if (transpose_csr(n, rp, ci, nv, &rpt, &cit, &nvt) != OR_OK) return -2;
+    int64_t it = or_cgnr(n, rp, ci, nv, rpt, cit, nvt, sigma, rhs, v, eps, maxit);
+    free(rpt); free(cit); free(nvt);
+    return it;
+}
+
+/* Wall-clock seconds, for the CPU baseline timing. */
+double or_wtime(void)
+{
+#ifdef _OPENMP
+    return omp_get_wtime();
+#else
+    return 0.0;
+#endif
+}
