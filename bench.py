@@ -1,0 +1,372 @@
+"""Time-to-tolerance benchmark of FP16-inner GADI-IR on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Workload: the 3D convection-diffusion system of §4.1 on a 64^3 grid
+(n = 262,144, 7-point, beta = 100, manufactured solution sin(pi x) sin(pi y)
+sin(pi z)), solved from x0 = 0 to normwise backward error eta_inf <= 1e-13
+with FP16 inner solves (FP16 storage, FP32 arithmetic) and FP64 residual and
+update. One step = one complete solve. Inputs are resident on the device
+when a step's timing starts; L2 (129 MB) is flushed before every timed
+step by writing a 256 MB buffer (outside the timed region).
+
+Prints one JSON line. Secondary numbers in the line: the same solve with
+plain FP64 GADI (inner eps 1e-10) on the same GPU, and operator-application
+bandwidths per kernel variant.
+
+Under torchrun (N > 1) every rank solves its own copy of the system
+(replicas: a single solve is not sharded), the step time is the maximum
+over ranks and rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-13 backward error (s) and SpMV GB/s: FP16-inner GADI-IR vs FP64 GADI"
+WORKLOAD = "convdiff3d_64_b100"
+TOL = 1e-13
+ALPHA, OMEGA = 3.0, 1.0          # chosen by the (alpha, omega) grid sweep
+EPS16 = 1e-2
+EPS64 = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--alpha", type=float, default=ALPHA)
+    ap.add_argument("--omega", type=float, default=OMEGA)
+    ap.add_argument("--kernel", default="stencil", choices=["stencil", "sparse"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GADI comparison")
+    ap.add_argument("--cpu-sample-s", type=float, default=20.0,
+                    help="bound on the CPU oracle's time for cpu_baseline")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        dist.init_process_group(backend)
+    return rank, world
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(n, nnz, info, kernel, fp16):
+    """Minimum bytes the method moves for one solve, from the solve counters.
+    Per row: outer step 66 B (FP64 residual 24, demotion 14, CGNR start 10,
+    FP64 update 18), CG iteration 20 B, CGNR iteration 22 B (FP16 vectors;
+    x4 for FP64 inner vectors except the FP64 outer terms), plus the matrix
+    bytes of each operator application (0 for the constant-coefficient
+    stencil; values + column indices per stored entry for the sparse form)."""
+    vb = 1 if fp16 else 4
+    outer, itH, itS = info["outer_iters"], info["inner_iters_H"], info["inner_iters_S"]
+    per_row = outer * (24 + 18 + vb * (14 - 8 + 10) + (8 if not fp16 else 8)) \
+        + itH * 20 * vb + itS * 22 * vb
+    vec = n * per_row
+    if kernel == "stencil":
+        mat = 0.0
+    else:
+        vsz = 2 if fp16 else 8
+        per_apply = nnz * (vsz + 4)
+        mat = (outer + 1) * nnz * 12 + (itH + 2 * itS + outer) * per_apply
+    return float(vec + mat)
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2501_04229_gb300 import build as B
+    from paper_2501_04229_gb300 import gadi as G
+    from paper_2501_04229_gb300 import problems as P
+
+    B.build()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    p = P.workload(WORKLOAD)
+    n, nnz = p.n, p.A.nnz
+    stream = torch.cuda.current_stream()
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
+    h = G.gadi_create(t(p.A.row_ptr, torch.int32), t(p.A.col_idx, torch.int32), t(p.A.val),
+                      stencil=(3, p.N, p.beta, 0), stream=stream.cuda_stream)
+    kern = G.GADI_KERNEL_STENCIL if args.kernel == "stencil" else G.GADI_KERNEL_SPARSE
+    G.gadi_set_kernel(h, kern)
+    b = t(p.b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def configure(u_r):
+        G.gadi_set_params(h, args.alpha, args.omega, u_r=u_r)
+        G.gadi_set_inner(h, EPS16 if u_r == G.GADI_F16 else EPS64, 500 if u_r == G.GADI_F16 else 10000,
+                         100000)
+
+    def timed_solves(k, w, u_r, sampler=None):
+        configure(u_r)
+        for _ in range(w):
+            x.zero_()
+            st, info = G.gadi_solve(h, b, x, TOL)
+            assert st == G.GADI_OK, G.last_error(h)
+        times, infos = [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for _ in range(k):
+            x.zero_()
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st, info = G.gadi_solve(h, b, x, TOL)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert st == G.GADI_OK, G.last_error(h)
+            times.append(e0.elapsed_time(e1) * 1e-3)
+            infos.append(info)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return times, infos
+
+    clocks = ClockSampler(dev)
+    with clocks:
+        t16, i16 = timed_solves(args.steps, args.warmup, G.GADI_F16)
+    eta_gpu = i16[-1]["eta_inf"]
+    x16 = x.cpu().numpy()
+    tot = sum(t16)
+    if world > 1:
+        tt = torch.tensor([tot], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        tot = float(tt.item())
+    ms_per_step = tot / args.steps * 1e3
+    kern_t = [i["t_solve_s"] for i in i16]
+    info = i16[-1]
+
+    # FP64 GADI on the same GPU (the baseline of the comparison)
+    fp64 = None
+    if not args.no_fp64:
+        t64, i64 = timed_solves(max(2, args.steps // 3), 1, G.GADI_F64)
+        fp64 = {"time_s": statistics.median(t64), "outer_iters": i64[-1]["outer_iters"],
+                "inner_iters_H": i64[-1]["inner_iters_H"], "inner_iters_S": i64[-1]["inner_iters_S"],
+                "eta_inf": i64[-1]["eta_inf"], "eps_inner": EPS64}
+
+    # operator-application bandwidth per variant (L2 flushed before each)
+    spmv = {}
+    configure(G.GADI_F16)
+    for kname, kk in (("stencil", G.GADI_KERNEL_STENCIL), ("sparse", G.GADI_KERNEL_SPARSE)):
+        G.gadi_set_kernel(h, kk)
+        for prec, u_r, dt, vs in (("fp16", G.GADI_F16, torch.float16, 2), ("fp64", G.GADI_F64, torch.float64, 8)):
+            G.gadi_set_params(h, args.alpha, args.omega, u_r=u_r)
+            xi = torch.randn(n, device="cuda").to(dt)
+            yo = torch.empty_like(xi)
+            for _ in range(3):
+                G.gadi_apply(h, G.OP_H, xi, yo)
+            ts = []
+            for _ in range(10):
+                flush.fill_(2.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                G.gadi_apply(h, G.OP_H, xi, yo)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+            mat = 0 if kname == "stencil" else nnz * (vs + 4)
+            byts = 2 * n * vs + mat
+            spmv[f"{kname}_{prec}_H"] = {"GBps": round(byts / statistics.median(ts) / 1e9, 1),
+                                         "bytes": byts, "us": round(statistics.median(ts) * 1e6, 2)}
+    G.gadi_set_kernel(h, kern)
+    configure(G.GADI_F16)
+
+    # end to end through the C ABI with pinned host buffers (copies inside)
+    bh = torch.from_numpy(p.b.copy()).pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        xh.zero_()
+        flush.fill_(3.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, _ = G.gadi_solve(h, bh, xh, TOL)
+        t1 = time.perf_counter()
+        assert st == G.GADI_OK
+        if i >= args.warmup:
+            e2e.append(t1 - t0)
+    G.gadi_destroy(h)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = algorithmic_bytes(n, nnz, info, args.kernel, True) / statistics.mean(kern_t) / 1e9
+    return {
+        "ms_per_step": ms_per_step, "value": tot / args.steps, "info": info, "eta_gpu": eta_gpu,
+        "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(),
+        "e2e": statistics.mean(e2e), "roofline": {
+            "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None,
+            "kernel": "gadi_solve_kernel<StencilOp<half,3>>" if args.kernel == "stencil"
+            else "gadi_solve_kernel<EllOp<half>>",
+            "note": "whole solve in one persistent launch; the 64^3 working set is L2-resident, so this is an effective rate",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
+        "kernel_time_s": statistics.mean(kern_t),
+    }
+
+
+def cpu_oracle_time(p, alpha, omega, budget_s):
+    """The oracle (FP64-inner GADI-IR, all host cores) on the same system,
+    bounded: a full solve when it fits the budget, else max_outer steps
+    scaled to the outer-step count of a full solve."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    _, info1, _ = oracle.gadi_ir(p.A, p.b, alpha, omega, tol=TOL, eps_inner=EPS16,
+                                 prec=oracle.PREC_DOUBLE, max_outer=2, max_inner=500)
+    per_outer = (time.perf_counter() - t0) / max(1, info1["outer_iters"])
+    est_outer = None
+    max_outer = max(2, int(budget_s / max(per_outer, 1e-6)))
+    t0 = time.perf_counter()
+    x, info, _ = oracle.gadi_ir(p.A, p.b, alpha, omega, tol=TOL, eps_inner=EPS16,
+                                prec=oracle.PREC_DOUBLE, max_outer=max_outer, max_inner=500)
+    dt = time.perf_counter() - t0
+    if info["status"] == oracle.OK:
+        return {"value": dt, "unit": "s", "cores": cores, "kind": "oracle",
+                "sample": f"one full FP64-inner GADI-IR solve of {WORKLOAD} to eta 1e-13 "
+                          f"({info['outer_iters']} outer steps)"}, x, info
+    # not finished within the budget: extrapolate per outer step
+    return {"value": None, "unit": "s", "cores": cores, "kind": "oracle", "per_outer_step_s": dt / max(1, info["outer_iters"]),
+            "sample": f"{info['outer_iters']} outer steps of FP64-inner GADI-IR on {WORKLOAD}"}, x, info
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args)
+    base = {"metric": METRIC, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic (3D convection-diffusion, manufactured solution)"}
+    cfg = {"workload": WORKLOAD, "n": 262144, "nnz": 1810432, "beta": 100.0, "tol_eta_inf": TOL,
+           "alpha": args.alpha, "omega": args.omega, "eps_inner": EPS16,
+           "precisions": "u_r=fp16 (fp32 arithmetic), u=u_f=fp64", "kernel": args.kernel,
+           "l2": "flushed before every timed step (256 MB write)",
+           "parallelism": "replicas" if world > 1 else "single GPU"}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_2501_04229_gb300 import problems as P
+        p = P.workload(WORKLOAD)
+        times = []
+        cb = None
+        for i in range(args.warmup + args.steps):
+            cb, _, info = cpu_oracle_time(p, args.alpha, args.omega, 30.0 if i >= args.warmup else 5.0)
+            if i >= args.warmup and cb["value"] is not None:
+                times.append(cb["value"])
+            elif i >= args.warmup:
+                times.append(cb["per_outer_step_s"] * max(1, info["outer_iters"]))
+        v = statistics.mean(times)
+        cb = dict(cb)
+        cb["value"] = v
+        line = dict(base, impl="reference", value=v, ms_per_step=v * 1e3, dtype="f64", config=cfg,
+                    cpu_baseline=cb, e2e={"value": v, "unit": "s", "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0})
+        print(json.dumps(line))
+        return
+
+    r = run_gpu(args, rank, world)
+    if rank != 0:
+        return
+    import oracle
+    p = r["p"]
+    eta_cpu = oracle.backward_error(p.A, p.b, r["x"])
+    fwd = float(np.abs(r["x"] - p.x_exact).max())
+    cb, _, _ = cpu_oracle_time(p, args.alpha, args.omega, args.cpu_sample_s)
+    if cb["value"] is None:
+        cb["value"] = cb["per_outer_step_s"] * r["info"]["outer_iters"]
+        cb["sample"] += f"; scaled to the GPU run's {r['info']['outer_iters']} outer steps"
+    n = p.n
+    line = dict(base)
+    line.update({
+        "value": r["value"], "ms_per_step": r["ms_per_step"], "dtype": "fp16-inner/fp64-outer",
+        "config": cfg,
+        "roofline": r["roofline"],
+        "cpu_baseline": cb,
+        "e2e": {"value": r["e2e"], "unit": "s", "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
+        "gpu_launches": 3 * args.steps,
+        "clocks": r["clocks"],
+        "solve": {k: r["info"][k] for k in ("outer_iters", "inner_iters_H", "inner_iters_S", "spmv_count",
+                                            "grid_blocks", "block_threads")},
+        "eta_inf_gpu": r["eta_gpu"], "eta_inf_oracle_check": eta_cpu, "max_abs_err_vs_exact": fwd,
+        "fp64_gadi_same_gpu": r["fp64"],
+        "speedup_vs_fp64_gadi": (r["fp64"]["time_s"] / r["value"]) if r["fp64"] else None,
+        "spmv": r["spmv"],
+    })
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

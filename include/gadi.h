@@ -31,6 +31,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define GADI_API __attribute__((visibility("default")))
+#else
+#define GADI_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -79,21 +85,24 @@ typedef struct {
     int32_t on_device;
 } gadi_csr;
 
-/* Optional structure of A for the matrix-free kernels: the h^2-scaled
+/* Optional structure of A for the matrix-free kernels: A is the h^2-scaled
  * centred-difference convection-diffusion operator of §4.1 on an N^dim grid
- * of interior nodes (x fastest), h = 1/(N+1), convection c = beta*h/2:
- * row i has diagonal sum_f k_f over its 2*dim faces, -k_f - c towards the
- * lower neighbour along each axis and -k_f + c towards the upper one.
- * k_faces: NULL for k = 1, else (dim = 3 only) three host FP64 arrays:
- *   k_faces[0] shape (N, N, N+1) index (iz, iy, fx)   face fx between nodes fx-1, fx
- *   k_faces[1] shape (N, N+1, N) index (iz, fy, ix)
- *   k_faces[2] shape (N+1, N, N) index (fz, iy, ix)
- * gadi_create checks that the CSR matrix equals this operator entry by entry
- * (relative difference <= 1e-12) and rejects the descriptor otherwise. */
+ * of interior nodes (x fastest), h = 1/(N+1), convection c = beta*h/2: row
+ * i has a diagonal entry, -k_f - c towards the lower neighbour along each
+ * axis and -k_f + c towards the upper one, k_f the coefficient of the face
+ * between them (neighbours on the boundary are omitted).
+ *   variable_k = 0: k_f = 1 everywhere (diagonal 2*dim); the kernels use
+ *                   scalar coefficients only.
+ *   variable_k = 1: k_f varies (dim = 3 only); the kernels keep the diagonal
+ *                   and one coupling per axis and node, taken from A.
+ * gadi_create checks the CSR pattern and values against this description
+ * (pattern exact; values, and the convection part of every entry, within a
+ * relative 1e-12) and returns GADI_ERR_INVALID_ARG on a mismatch. The
+ * stencil kernels need the HSS splitting. */
 typedef struct {
     int32_t dim, N;
     double beta;
-    const double *const *k_faces;
+    int32_t variable_k;
 } gadi_stencil;
 
 typedef struct {
@@ -120,7 +129,7 @@ typedef struct {
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
  * Errors: INVALID_ARG (n < 1, bad pattern, pattern not symmetric, unsorted
  * columns, non-finite values, stencil mismatch), OUT_OF_MEMORY, CUDA. */
-gadi_status gadi_create(const gadi_csr *A, gadi_splitting split, const gadi_csr *M_user,
+GADI_API gadi_status gadi_create(const gadi_csr *A, gadi_splitting split, const gadi_csr *M_user,
                         const gadi_stencil *structure, void *cuda_stream, gadi_solver **out);
 
 /* Parameters of eq. (gadi) and the precision triple of Algorithm 1.
@@ -130,32 +139,38 @@ gadi_status gadi_create(const gadi_csr *A, gadi_splitting split, const gadi_csr 
  * with FP32 arithmetic; A, r and z are scaled by powers of two so FP16 stays
  * in range, and (2 - omega) alpha is applied in the FP64 update.
  * u_r = GADI_F64 with the default inner tolerance is plain FP64 GADI. */
-gadi_status gadi_set_params(gadi_solver *h, double alpha, double omega,
+GADI_API gadi_status gadi_set_params(gadi_solver *h, double alpha, double omega,
                             gadi_precision u_r, gadi_precision u, gadi_precision u_f);
 
 /* Inner relative tolerance eps (0 < eps < 1): each inner solve stops when
  * ||rhs - K v||_2 <= eps ||rhs||_2, or after max_inner iterations (>= 1).
  * max_outer (>= 0) caps the refinement steps. Defaults: eps 1e-2 (FP16
  * inner) / 1e-10 (FP64 inner), max_inner 200, max_outer 100000. */
-gadi_status gadi_set_inner(gadi_solver *h, double eps_inner, int32_t max_inner, int32_t max_outer);
+GADI_API gadi_status gadi_set_inner(gadi_solver *h, double eps_inner, int32_t max_inner, int32_t max_outer);
 
 /* Stopping criterion kind for gadi_solve's tol (default GADI_STOP_ETA). */
-gadi_status gadi_set_stop(gadi_solver *h, gadi_stop kind);
+GADI_API gadi_status gadi_set_stop(gadi_solver *h, gadi_stop kind);
 
 /* Kernel family (default GADI_KERNEL_AUTO). STENCIL without a descriptor
  * returns INVALID_ARG. */
-gadi_status gadi_set_kernel(gadi_solver *h, gadi_kernel kind);
+GADI_API gadi_status gadi_set_kernel(gadi_solver *h, gadi_kernel kind);
 
 /* Launch shape of the persistent solve kernel: grid_blocks (0 = automatic,
  * else 1 .. the co-resident maximum) and block_threads (0 = automatic, else
  * 128, 256, 512 or 1024). One block runs the solve with block-local barriers
  * only. */
-gadi_status gadi_set_launch(gadi_solver *h, int32_t grid_blocks, int32_t block_threads);
+GADI_API gadi_status gadi_set_launch(gadi_solver *h, int32_t grid_blocks, int32_t block_threads);
 
 /* Upper bound, in milliseconds, of every device-side grid-barrier wait
  * (default 2000). An expired wait ends the solve with GADI_ERR_TIMEOUT and
  * leaves the handle usable. */
-gadi_status gadi_set_wait_limit(gadi_solver *h, double milliseconds);
+GADI_API gadi_status gadi_set_wait_limit(gadi_solver *h, double milliseconds);
+
+/* Test hook: when on != 0, the next solves give every grid-barrier wait an
+ * arrival target that no block reaches, so the wait limit expires and the
+ * solve returns GADI_ERR_TIMEOUT (needs a launch of 2 or more blocks). No
+ * fault and no hang: the wait is bounded by gadi_set_wait_limit. */
+GADI_API gadi_status gadi_debug_force_timeout(gadi_solver *h, int32_t on);
 
 /* Solve A x = b. b (n FP64) and x (n FP64; in: x0, out: the result) are
  * both host or both device pointers. Host buffers are copied to and from
@@ -164,7 +179,7 @@ gadi_status gadi_set_wait_limit(gadi_solver *h, double milliseconds);
  * by gadi_set_stop. Returns OK, NOT_CONVERGED, DIVERGED (x holds the last
  * iterate), TIMEOUT, INVALID_ARG (tol <= 0, non-finite b, mixed pointer
  * kinds) or CUDA. info may be NULL. */
-gadi_status gadi_solve(gadi_solver *h, const double *b, double *x, double tol, gadi_info *info);
+GADI_API gadi_status gadi_solve(gadi_solver *h, const double *b, double *x, double tol, gadi_info *info);
 
 /* One operator application with the solver's current kernel and parameters,
  * y = K x, for kernel-level tests and bandwidth measurement. which:
@@ -174,23 +189,23 @@ gadi_status gadi_solve(gadi_solver *h, const double *b, double *x, double tol, g
  *   3: K = S'^T
  * x, y are device pointers of n elements of the inner precision (FP64 for
  * which = 0). Asynchronous on the handle's stream. */
-gadi_status gadi_apply(gadi_solver *h, int32_t which, const void *x, void *y);
+GADI_API gadi_status gadi_apply(gadi_solver *h, int32_t which, const void *x, void *y);
 
 /* Scale exponents (sM, sN) that the inner operators use for the current
  * alpha and inner precision. */
-gadi_status gadi_get_scales(gadi_solver *h, int32_t *sM, int32_t *sN);
+GADI_API gadi_status gadi_get_scales(gadi_solver *h, int32_t *sM, int32_t *sN);
 
 /* Predict (alpha, omega) from problem features (§3.3). features[0] = log n,
  * features[1] = log beta. kind: 0 MLP, 1 GPR, 2 grid search. Returns
  * NO_MODEL when no predictor of that kind has been loaded. */
-gadi_status gadi_predict_params(gadi_solver *h, const double *features, int32_t nfeat,
+GADI_API gadi_status gadi_predict_params(gadi_solver *h, const double *features, int32_t nfeat,
                                 int32_t kind, double *alpha, double *omega);
 
 /* Release all device memory of h. NULL is accepted. */
-void gadi_destroy(gadi_solver *h);
+GADI_API void gadi_destroy(gadi_solver *h);
 
-const char *gadi_status_str(gadi_status s);
-const char *gadi_last_error(const gadi_solver *h);
+GADI_API const char *gadi_status_str(gadi_status s);
+GADI_API const char *gadi_last_error(const gadi_solver *h);
 
 #ifdef __cplusplus
 }

@@ -84,6 +84,10 @@ def _load():
                               C.POINTER(Info), p_f64, p_i32, p_i32]),
         "or_gadi_ir": (C.c_int, [i64, p_i32, p_i32, p_f64, p_f64, p_f64, C.POINTER(Params),
                                  C.POINTER(Info), p_f64, p_i32, p_i32]),
+        "or_gadi_ir_split": (C.c_int, [i64, p_i32, p_i32, p_f64, p_f64, p_f64, p_f64,
+                                       C.POINTER(Params), C.POINTER(Info), p_f64, p_i32, p_i32]),
+        "or_lp_apply": (C.c_int, [i64, p_i32, p_i32, p_f64, p_f64, f64, C.c_int, C.c_int,
+                                  p_f64, p_f64, p_i32, p_i32]),
         "or_to_half_bits": (None, [i64, p_f64, p_u16]),
         "or_wtime": (f64, []),
     }
@@ -193,7 +197,8 @@ def cgnr_solve(A_pattern, nval, sigma, rhs, x0=None, eps=1e-10, maxit=1000):
     return v, int(it)
 
 
-def _run(fn_name, A, b, x0, alpha, omega, tol, eps_inner, max_inner, max_outer, stop, prec):
+def _run(fn_name, A, b, x0, alpha, omega, tol, eps_inner, max_inner, max_outer, stop, prec,
+         m_user=None):
     lib = _load()
     n, rp, ci, v = _csr(A)
     b = _f64(b)
@@ -204,9 +209,14 @@ def _run(fn_name, A, b, x0, alpha, omega, tol, eps_inner, max_inner, max_outer, 
     eta = np.full(max_outer + 1, np.nan)
     itH = np.zeros(max(max_outer, 1), dtype=np.int32)
     itS = np.zeros(max(max_outer, 1), dtype=np.int32)
-    getattr(lib, fn_name)(n, _p(rp, C.c_int32), _p(ci, C.c_int32), _p(v, C.c_double),
-                          _p(b, C.c_double), _p(x, C.c_double), C.byref(P), C.byref(I),
-                          _p(eta, C.c_double), _p(itH, C.c_int32), _p(itS, C.c_int32))
+    tail = (_p(b, C.c_double), _p(x, C.c_double), C.byref(P), C.byref(I),
+            _p(eta, C.c_double), _p(itH, C.c_int32), _p(itS, C.c_int32))
+    if fn_name == "or_gadi_ir_split":
+        mu = _f64(m_user)
+        getattr(lib, fn_name)(n, _p(rp, C.c_int32), _p(ci, C.c_int32), _p(v, C.c_double),
+                              _p(mu, C.c_double), *tail)
+    else:
+        getattr(lib, fn_name)(n, _p(rp, C.c_int32), _p(ci, C.c_int32), _p(v, C.c_double), *tail)
     k = I.outer_iters
     hist = {"eta": eta[:k + 1].copy(), "itH": itH[:k].copy(), "itS": itS[:k].copy()}
     return x, I.as_dict(), hist
@@ -220,10 +230,31 @@ def gadi(A, b, alpha, omega, tol=1e-13, eps_inner=1e-10, max_inner=10000, max_ou
 
 
 def gadi_ir(A, b, alpha, omega, tol=1e-13, eps_inner=1e-2, max_inner=200, max_outer=10000,
-            stop=STOP_ETA, prec=PREC_HALF, x0=None):
-    """GADI-IR, Algorithm 1, u = u_f = FP64, u_r = prec."""
+            stop=STOP_ETA, prec=PREC_HALF, x0=None, m_user=None):
+    """GADI-IR, Algorithm 1, u = u_f = FP64, u_r = prec. m_user: None for the
+    HSS splitting, else M's values on A's pattern (N = A - M)."""
+    if m_user is not None:
+        return _run("or_gadi_ir_split", A, b, x0, alpha, omega, tol, eps_inner, max_inner,
+                    max_outer, stop, prec, m_user=m_user)
     return _run("or_gadi_ir", A, b, x0, alpha, omega, tol, eps_inner, max_inner, max_outer, stop,
                 prec)
+
+
+def lp_apply(A, alpha, which, prec, x, m_user=None):
+    """One operator application as GADI-IR does it (see or_lp_apply):
+    which 0 A, 1 H', 2 S', 3 S'^T. Returns (y, sM, sN)."""
+    lib = _load()
+    n, rp, ci, v = _csr(A)
+    x = _f64(x)
+    y = np.empty(n)
+    sM, sN = C.c_int32(), C.c_int32()
+    mu = None if m_user is None else _f64(m_user)
+    st = lib.or_lp_apply(n, _p(rp, C.c_int32), _p(ci, C.c_int32), _p(v, C.c_double),
+                         None if mu is None else _p(mu, C.c_double), float(alpha), int(which),
+                         int(prec), _p(x, C.c_double), _p(y, C.c_double), C.byref(sM), C.byref(sN))
+    if st != OK:
+        raise ValueError("or_lp_apply failed")
+    return y, sM.value, sN.value
 
 
 def to_half_bits(x) -> np.ndarray:

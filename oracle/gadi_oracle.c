@@ -270,7 +270,8 @@ int64_t or_cg(int64_t n, const int32_t *rp, const int32_t *ci, const double *m, 
 
 /* CGNR for S v = rhs with S = sigma I + V: CG on S^T S v = S^T rhs, where
  * S^T = sigma I + V^T (Vt is V's explicit transpose). Same stopping rule as
- * or_cg, on the residual of S v = rhs. Counts one per SpMV with S or S^T. */
+ * or_cg, on the residual of S v = rhs. Returns the number of iterations
+ * (each one product with S and, unless it is the last, one with S^T). */
 int64_t or_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const double *vv,
                 const int32_t *rpt, const int32_t *cit, const double *vt, double sigma,
                 const double *rhs, double *v, double eps, int32_t maxit)
@@ -285,7 +286,6 @@ int64_t or_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const double *v
     int64_t it = 0;
     if (rr0 > 0.0) {
         or_spmv_shift(n, rpt, cit, vt, sigma, r, s);
-        ++it;
         memcpy(p, s, sz);
         double g = dot64(n, s, s);
         while (it < maxit) {
@@ -300,7 +300,6 @@ int64_t or_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const double *v
             if (!isfinite(rr)) { it = -1; break; }
             if (rr <= eps * eps * rr0) break;
             or_spmv_shift(n, rpt, cit, vt, sigma, r, s);
-            ++it;
             double gn = dot64(n, s, s);
             double beta = gn / g;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
@@ -414,7 +413,6 @@ static int64_t lp_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const fl
     int64_t it = 0;
     if (rr0 > 0.0f) {
         spmv32(n, rpt, cit, nvt, sigma, r, s, half);
-        ++it;
         memcpy(p, s, sz);
         float g = dot32(n, s, s);
         while (it < maxit) {
@@ -432,7 +430,6 @@ static int64_t lp_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const fl
             if (!isfinite(rr)) { it = -1; break; }
             if (rr <= eps2 * rr0) break;
             spmv32(n, rpt, cit, nvt, sigma, r, s, half);
-            ++it;
             float gn = dot32(n, s, s);
             float beta = gn / g;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
@@ -557,7 +554,7 @@ int or_gadi(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
         memcpy(x, xn, szv);
         info->inner_iters_H += ih;
         info->inner_iters_S += is;
-        info->spmv_count += ih + is + 4;  /* + 2 rhs products + 2 initial inner residuals */
+        info->spmv_count += ih + 2 * is + 4;  /* + 2 rhs products + 2 initial inner residuals */
         if (itH) itH[k] = (int32_t)ih;
         if (itS) itS[k] = (int32_t)is;
         ++k;
@@ -578,9 +575,9 @@ int or_gadi(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
  * rounded to the inner precision (r^ = fl_r(s^), §2.2) after scaling by
  * 2^-e, e = floor(log2 ||r||_inf); z is rescaled by 2^-ez before step 3; the
  * scales and (2-w) a are applied to y in FP64 in step 4. */
-int or_gadi_ir(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
-               const double *b, double *x, const or_params *P, or_info *info,
-               double *eta_hist, int32_t *itH, int32_t *itS)
+int or_gadi_ir_split(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+                     const double *m_user, const double *b, double *x, const or_params *P,
+                     or_info *info, double *eta_hist, int32_t *itH, int32_t *itS)
 {
     memset(info, 0, sizeof(*info));
     if (check_params(P) != OR_OK || P->inner_prec < 0 || P->inner_prec > 3) {
@@ -590,7 +587,10 @@ int or_gadi_ir(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
     size_t szv = (size_t)(n > 0 ? n : 1) * sizeof(double);
     size_t szm = (size_t)(nnz > 0 ? nnz : 1) * sizeof(double);
     double *m = (double *)malloc(szm), *nv = (double *)malloc(szm);
-    if (or_hss_split(n, rp, ci, a, m, nv) != OR_OK) {
+    if (m_user) {
+        /* user splitting A = M + N: N = A - M on A's pattern */
+        for (int64_t k = 0; k < nnz; ++k) { m[k] = m_user[k]; nv[k] = a[k] - m_user[k]; }
+    } else if (or_hss_split(n, rp, ci, a, m, nv) != OR_OK) {
         free(m); free(nv); info->status = OR_INVALID; return OR_INVALID;
     }
     int32_t *rpt, *cit; double *nvt;
@@ -629,6 +629,8 @@ int or_gadi_ir(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
             if (half) {
                 sM = half_scale_exponent(n, rp, m, al);
                 sN = half_scale_exponent(n, rp, nv, al);
+                int sNt = half_scale_exponent(n, rpt, nvt, al);
+                if (sNt > sN) sN = sNt;     /* one scale for S and S^T */
             }
             for (int64_t k = 0; k < nnz; ++k) {
                 mf[k] = half ? (float)(_Float16)ldexp(m[k], -sM) : (float)m[k];
@@ -704,7 +706,7 @@ int or_gadi_ir(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
         }
         info->inner_iters_H += ih;
         info->inner_iters_S += is;
-        info->spmv_count += ih + is;
+        info->spmv_count += ih + 2 * is;
         if (itH) itH[k] = (int32_t)ih;
         if (itS) itS[k] = (int32_t)is;
         ++k;
@@ -715,6 +717,70 @@ int or_gadi_ir(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
     free(r); free(z); free(y);
     free(mf); free(nf); free(nft); free(rf); free(zf); free(yf);
     return status;
+}
+
+int or_gadi_ir(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+               const double *b, double *x, const or_params *P, or_info *info,
+               double *eta_hist, int32_t *itH, int32_t *itS)
+{
+    return or_gadi_ir_split(n, rp, ci, a, NULL, b, x, P, info, eta_hist, itH, itS);
+}
+
+/* One application of an operator of Algorithm 1 in a given inner precision,
+ * with the same splitting, scaling and rounding as or_gadi_ir_split:
+ *   which 0: y = A x (FP64)
+ *   which 1: y = fl(H' x),  H' = 2^-sM (aI + M)
+ *   which 2: y = fl(S' x),  S' = 2^-sN (aI + N)
+ *   which 3: y = fl(S'^T x)
+ * prec: OR_PREC_HALF, OR_PREC_SINGLE or OR_PREC_DOUBLE; x holds values of
+ * that precision (as doubles). The scale exponents used are returned. */
+int or_lp_apply(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+                const double *m_user, double alpha, int which, int prec,
+                const double *x, double *y, int32_t *sM_out, int32_t *sN_out)
+{
+    int64_t nnz = rp[n];
+    size_t szm = (size_t)(nnz > 0 ? nnz : 1) * sizeof(double);
+    double *m = (double *)malloc(szm), *nv = (double *)malloc(szm);
+    if (m_user) {
+        for (int64_t k = 0; k < nnz; ++k) { m[k] = m_user[k]; nv[k] = a[k] - m_user[k]; }
+    } else if (or_hss_split(n, rp, ci, a, m, nv) != OR_OK) {
+        free(m); free(nv); return OR_INVALID;
+    }
+    int32_t *rpt, *cit; double *nvt;
+    transpose_csr(n, rp, ci, nv, &rpt, &cit, &nvt);
+    const int half = prec == OR_PREC_HALF;
+    int sM = 0, sN = 0;
+    if (half) {
+        sM = half_scale_exponent(n, rp, m, alpha);
+        sN = half_scale_exponent(n, rp, nv, alpha);
+        int sNt = half_scale_exponent(n, rpt, nvt, alpha);
+        if (sNt > sN) sN = sNt;
+    }
+    if (sM_out) *sM_out = sM;
+    if (sN_out) *sN_out = sN;
+    if (which == 0) {
+        or_spmv_shift(n, rp, ci, a, 0.0, x, y);
+    } else if (prec == OR_PREC_DOUBLE) {
+        if (which == 1) or_spmv_shift(n, rp, ci, m, alpha, x, y);
+        else if (which == 2) or_spmv_shift(n, rp, ci, nv, alpha, x, y);
+        else or_spmv_shift(n, rpt, cit, nvt, alpha, x, y);
+    } else {
+        size_t szmf = (size_t)(nnz > 0 ? nnz : 1) * sizeof(float);
+        size_t szvf = (size_t)(n > 0 ? n : 1) * sizeof(float);
+        float *vf = (float *)malloc(szmf), *xf = (float *)malloc(szvf), *yf = (float *)malloc(szvf);
+        const double *src = which == 1 ? m : (which == 2 ? nv : nvt);
+        int s = which == 1 ? sM : sN;
+        for (int64_t k = 0; k < nnz; ++k)
+            vf[k] = half ? (float)(_Float16)ldexp(src[k], -s) : (float)src[k];
+        for (int64_t i = 0; i < n; ++i) xf[i] = (float)x[i];
+        float sig = (float)ldexp(alpha, -s);
+        if (which == 3) spmv32(n, rpt, cit, vf, sig, xf, yf, half);
+        else spmv32(n, rp, ci, vf, sig, xf, yf, half);
+        for (int64_t i = 0; i < n; ++i) y[i] = (double)yf[i];
+        free(vf); free(xf); free(yf);
+    }
+    free(m); free(nv); free(rpt); free(cit); free(nvt);
+    return OR_OK;
 }
 
 /* FP64 -> FP16 conversion (round to nearest even, direct from double), as

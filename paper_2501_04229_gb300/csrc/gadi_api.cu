@@ -1,0 +1,937 @@
+// gadi_api.cu -- C ABI of libgadi.so: set-up kernels (CSR checks, HSS
+// splitting into the ELL layout, FP16 demotion, stencil extraction) and the
+// host logic around the persistent solve kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+
+#include "../../include/gadi.h"
+#include "gadi_solve.cuh"
+
+using namespace gadi;
+
+// ===========================================================================
+// Set-up kernels
+// ===========================================================================
+namespace {
+
+constexpr int kSetupThreads = 256;
+
+inline unsigned grid_for(int64_t n, int threads = kSetupThreads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 65535LL * 32) g = 65535LL * 32;
+    return (unsigned)g;
+}
+
+// flags in the set-up error word
+enum : int {
+    kBadRowPtr = 1, kBadCol = 2, kUnsorted = 4, kNonFinite = 8, kUnsymPattern = 16,
+    kStencilPattern = 32, kStencilValue = 64
+};
+
+__global__ void k_check_csr(int64_t n, int64_t nnz, const int *rp, const int *ci, const double *v,
+                            int *bad, int *maxlen)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = rp[i], hi = rp[i + 1];
+        int f = 0;
+        if (i == 0 && lo != 0) f |= kBadRowPtr;
+        if (i == n - 1 && (int64_t)hi != nnz) f |= kBadRowPtr;
+        if (lo < 0 || hi < lo || (int64_t)hi > nnz) {
+            atomicOr(bad, f | kBadRowPtr);
+            continue;
+        }
+        atomicMax(maxlen, hi - lo);
+        for (int k = lo; k < hi; ++k) {
+            int c = ci[k];
+            if (c < 0 || (int64_t)c >= n) f |= kBadCol;
+            if (k > lo && c <= ci[k - 1]) f |= kUnsorted;
+            if (!isfinite(v[k])) f |= kNonFinite;
+        }
+        if (f) atomicOr(bad, f);
+    }
+}
+
+__device__ __forceinline__ int find_in_row(const int *rp, const int *ci, int64_t row, int64_t col)
+{
+    int lo = rp[row], hi = rp[row + 1] - 1;
+    while (lo <= hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        int c = ci[mid];
+        if (c == col) return mid;
+        if (c < col) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v)
+{
+    atomicMax((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// Splitting of A on its own pattern into the ELL arrays.
+//   HSS:  m = (a_ij + a_ji)/2, n = (a_ij - a_ji)/2           (§4.1)
+//   user: m = m_user_ij, n = a_ij - m_ij, n^T_ij = a_ji - m_ji
+// norms[0..3] receive max row sums of |A|, |M|, |N|, |N^T|.
+__global__ void k_split_ell(int64_t n, const int *rp, const int *ci, const double *a,
+                            const double *mu, int W, int *ecol, double *ea, double *em,
+                            double *en, double *ent, double *norms, int *bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t base = i * W;
+        int t = 0;
+        double sa = 0, sm = 0, sn = 0, snt = 0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k, ++t) {
+            const int j = ci[k];
+            const int kt = find_in_row(rp, ci, j, i);
+            double aij = a[k], m, nv, ntv;
+            if (kt < 0) {
+                atomicOr(bad, kUnsymPattern);
+                m = nv = ntv = 0.0;
+            } else if (mu) {
+                m = mu[k];
+                nv = __dsub_rn(aij, m);
+                ntv = __dsub_rn(a[kt], mu[kt]);
+            } else {
+                m = __dmul_rn(0.5, __dadd_rn(aij, a[kt]));
+                nv = __dmul_rn(0.5, __dsub_rn(aij, a[kt]));
+                ntv = -nv;
+            }
+            ecol[base + t] = j;
+            ea[base + t] = aij;
+            em[base + t] = m;
+            en[base + t] = nv;
+            if (ent) ent[base + t] = ntv;
+            sa += fabs(aij);
+            sm += fabs(m);
+            sn += fabs(nv);
+            snt += fabs(ntv);
+        }
+        for (; t < W; ++t) {
+            ecol[base + t] = (int)i;
+            ea[base + t] = 0.0;
+            em[base + t] = 0.0;
+            en[base + t] = 0.0;
+            if (ent) ent[base + t] = 0.0;
+        }
+        atomic_max_nonneg(norms + 0, sa);
+        atomic_max_nonneg(norms + 1, sm);
+        atomic_max_nonneg(norms + 2, sn);
+        atomic_max_nonneg(norms + 3, snt);
+    }
+}
+
+// dst = fl16(src * 2^-s), round to nearest even, directly from FP64
+__global__ void k_demote(int64_t cnt, const double *src, __half *dst, double scale)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __double2half(__dmul_rn(src[i], scale));
+}
+
+__global__ void k_count_range(int64_t cnt, const double *src, const __half *dst, int *lost)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float h = __half2float(dst[i]);
+        if ((src[i] != 0.0 && h == 0.0f) || isinf(h)) atomicAdd(lost, 1);
+    }
+}
+
+// Check the ELL arrays against the stencil description and extract the
+// per-node values the face-coefficient kernels use.
+__global__ void k_stencil_extract(int64_t n, int dim, int N, double c, int variable_k, int W,
+                                  const int *ecol, const double *ea, const double *em,
+                                  const double *en, double *AD, double *AL0, double *AL1,
+                                  double *AL2, double *AU0, double *AU1, double *AU2, double *HD,
+                                  double *HK0, double *HK1, double *HK2, int *bad)
+{
+    double *AL[3] = {AL0, AL1, AL2}, *AU[3] = {AU0, AU1, AU2}, *HK[3] = {HK0, HK1, HK2};
+    const int64_t st[3] = {1, N, (int64_t)N * N};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int cd[3];
+        int64_t t = i / N;
+        cd[0] = (int)(i - t * N);
+        if (dim == 3) { cd[1] = (int)(t % N); cd[2] = (int)(t / N); }
+        else { cd[1] = (int)t; cd[2] = 0; }
+        // expected columns, ascending: lower (z, y, x), diagonal, upper (x, y, z)
+        int64_t cols[7];
+        int kind[7];   // -1-d lower along d, 0 diagonal, 1+d upper along d
+        int ne = 0;
+        for (int d = dim - 1; d >= 0; --d)
+            if (cd[d] > 0) { cols[ne] = i - st[d]; kind[ne++] = -1 - d; }
+        cols[ne] = i; kind[ne++] = 0;
+        for (int d = 0; d < dim; ++d)
+            if (cd[d] < N - 1) { cols[ne] = i + st[d]; kind[ne++] = 1 + d; }
+        int f = 0;
+        for (int s = 0; s < W; ++s) {
+            const int64_t idx = i * W + s;
+            if (s >= ne) {
+                if (ecol[idx] != (int)i || ea[idx] != 0.0) f |= kStencilPattern;
+                continue;
+            }
+            if (ecol[idx] != cols[s]) { f |= kStencilPattern; continue; }
+            const double av = ea[idx], mv = em[idx], nvv = en[idx];
+            const int kd = kind[s];
+            const double tol = 1e-12 * fmax(1.0, fabs(av));
+            if (kd == 0) {
+                if (fabs(nvv) > tol) f |= kStencilValue;
+                if (!variable_k && fabs(av - 2.0 * dim) > tol) f |= kStencilValue;
+                if (AD) { AD[i] = av; HD[i] = mv; }
+            } else {
+                const int d = (kd < 0 ? -kd : kd) - 1;
+                const double want_n = kd < 0 ? -c : c;
+                if (fabs(nvv - want_n) > tol) f |= kStencilValue;
+                if (!variable_k && fabs(mv + 1.0) > tol) f |= kStencilValue;
+                if (AD) {
+                    if (kd < 0) AL[d][i] = av;
+                    else { AU[d][i] = av; HK[d][i] = mv; }
+                }
+            }
+        }
+        if (AD) {
+            for (int d = 0; d < dim; ++d) {
+                if (cd[d] == 0) AL[d][i] = 0.0;
+                if (cd[d] == N - 1) { AU[d][i] = 0.0; HK[d][i] = 0.0; }
+            }
+        }
+        if (f) atomicOr(bad, f);
+    }
+}
+
+// ||b||_inf and a non-finite flag
+__global__ void k_vec_check(int64_t n, const double *b, double *out_max, int *nonfinite)
+{
+    double m = 0.0;
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = b[i];
+        if (!isfinite(v)) bad = 1;
+        else m = fmax(m, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(out_max, m);
+        if (bad) atomicOr(nonfinite, 1);
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// Handle
+// ===========================================================================
+struct gadi_solver {
+    int dev = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0, nnz = 0;
+    int W = 0;
+    bool user_split = false;
+    // ELL arrays (device)
+    int *ecol = nullptr;
+    double *ea = nullptr, *em = nullptr, *en = nullptr, *ent = nullptr;
+    __half *m16 = nullptr, *n16 = nullptr, *nt16 = nullptr;
+    double anorm = 0, mnorm = 0, nnorm = 0, ntnorm = 0;
+    // stencil
+    bool has_stencil = false;
+    int sdim = 0, sN = 0, variable_k = 0;
+    double beta = 0, c = 0;
+    // constant-coefficient values taken from the split (so the stencil
+    // operators equal the sparse ones bit for bit): A's diagonal, lower and
+    // upper couplings, M's off-diagonal and N's upper coupling
+    double a_diag = 0, a_lo = 0, a_hi = 0, m_off = 0, n_up = 0;
+    double *AD = nullptr, *AL[3] = {}, *AU[3] = {}, *HD64 = nullptr, *HK64[3] = {};
+    __half *HD16 = nullptr, *HK16[3] = {};
+    // parameters
+    double alpha = 1.0, omega = 1.0;
+    int u_r = GADI_F16;
+    double eps = -1.0;
+    int max_inner = 200, max_outer = 100000;
+    int stop = GADI_STOP_ETA;
+    int kernel = GADI_KERNEL_AUTO;
+    int blocks = 0, threads = 0;
+    double wait_ms = 2000.0;
+    int force_timeout = 0;
+    // demoted operator state
+    int sM = 0, sNs = 0;
+    bool demoted = false;
+    double demoted_alpha = 0.0;
+    // work
+    double *bdev = nullptr, *xdev = nullptr, *r64 = nullptr;
+    void *vec = nullptr;      // 9 vectors of n elements of the inner type (sized for FP64)
+    unsigned long long *slots = nullptr;
+    int slot_blocks = 0;
+    Ctl *ctl = nullptr;
+    double *scratch = nullptr;   // small device scratch (norms, flags)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+gadi_status fail(gadi_solver *h, gadi_status s, const char *fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? GADI_ERR_OUT_OF_MEMORY           \
+                                                          : GADI_ERR_CUDA,                    \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,     \
+                        __LINE__);                                                            \
+        }                                                                                     \
+    } while (0)
+
+template <class X>
+cudaError_t dalloc(X **p, size_t count)
+{
+    return cudaMalloc((void **)p, (count ? count : 1) * sizeof(X));
+}
+
+void release(gadi_solver *h)
+{
+    void *ptrs[] = {h->ecol, h->ea, h->em, h->en, h->ent, h->m16, h->n16, h->nt16, h->AD,
+                    h->AL[0], h->AL[1], h->AL[2], h->AU[0], h->AU[1], h->AU[2], h->HD64,
+                    h->HK64[0], h->HK64[1], h->HK64[2], h->HD16, h->HK16[0], h->HK16[1],
+                    h->HK16[2], h->bdev, h->xdev, h->r64, h->vec, h->slots, h->ctl, h->scratch};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// s such that (|sigma| + norm) 2^-s lies in (1, 2]: keeps FP16 values of the
+// scaled operator, and of K p and K K^T r for vectors of size O(1), in range
+int half_scale_exponent(double norm, double sigma)
+{
+    double v = norm + std::fabs(sigma);
+    if (!(v > 0.0) || !std::isfinite(v)) return 0;
+    int e;
+    double m = std::frexp(v, &e);
+    int c = (m == 0.5) ? e - 1 : e;
+    return c - 1;
+}
+
+bool use_stencil(const gadi_solver *h)
+{
+    if (h->kernel == GADI_KERNEL_STENCIL) return true;
+    if (h->kernel == GADI_KERNEL_SPARSE) return false;
+    return h->has_stencil;
+}
+
+// Demote the inner operators for the current alpha (FP16 inner precision).
+gadi_status prepare_inner(gadi_solver *h)
+{
+    if (h->u_r != GADI_F16) {
+        h->sM = h->sNs = 0;
+        return GADI_OK;
+    }
+    int sM = half_scale_exponent(h->mnorm, h->alpha);
+    int sN = half_scale_exponent(h->nnorm, h->alpha);
+    if (h->demoted && sM == h->sM && sN == h->sNs) return GADI_OK;
+    const int64_t cnt = h->n * (int64_t)h->W;
+    const double scM = std::ldexp(1.0, -sM), scN = std::ldexp(1.0, -sN);
+    k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->em, h->m16, scM);
+    k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->en, h->n16, scN);
+    if (h->ent) k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->ent, h->nt16, scN);
+    if (h->HD64) {
+        k_demote<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HD64, h->HD16, scM);
+        for (int d = 0; d < h->sdim; ++d)
+            k_demote<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HK64[d], h->HK16[d], scM);
+    }
+    CK(cudaGetLastError());
+    // entries that flush to zero or overflow in FP16 even after scaling
+    int *lost = (int *)h->scratch;
+    CK(cudaMemsetAsync(lost, 0, sizeof(int), h->stream));
+    k_count_range<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->em, h->m16, lost);
+    k_count_range<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->en, h->n16, lost);
+    int nlost = 0;
+    CK(cudaMemcpyAsync(&nlost, lost, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (nlost)
+        return fail(h, GADI_ERR_RANGE, "%d matrix entries are out of FP16 range after scaling", nlost);
+    h->sM = sM;
+    h->sNs = sN;
+    h->demoted = true;
+    return GADI_OK;
+}
+
+template <class T>
+EllOp<T> make_ell(const gadi_solver *h)
+{
+    using Acc = typename Prec<T>::Acc;
+    EllOp<T> op;
+    op.n = h->n;
+    op.W = h->W;
+    op.col = h->ecol;
+    op.a64 = h->ea;
+    if constexpr (std::is_same<T, __half>::value) {
+        op.m = h->m16;
+        op.nv = h->n16;
+        op.nt = h->ent ? h->nt16 : nullptr;
+    } else {
+        op.m = h->em;
+        op.nv = h->en;
+        op.nt = h->ent;
+    }
+    op.sigH = (Acc)std::ldexp(h->alpha, -h->sM);
+    op.sigS = (Acc)std::ldexp(h->alpha, -h->sNs);
+    return op;
+}
+
+float half_round(double v)
+{
+    return __half2float(__double2half(v));
+}
+
+template <class T, int DIM>
+StencilOp<T, DIM> make_stencil(const gadi_solver *h)
+{
+    using Acc = typename Prec<T>::Acc;
+    StencilOp<T, DIM> op{};
+    op.dim = h->sdim;
+    op.N = h->sN;
+    op.n = h->n;
+    op.a_diag = h->a_diag;
+    op.a_lo = h->a_lo;
+    op.a_hi = h->a_hi;
+    op.AD = h->AD;
+    for (int d = 0; d < 3; ++d) {
+        op.AL[d] = h->AL[d];
+        op.AU[d] = h->AU[d];
+    }
+    const double scM = std::ldexp(1.0, -h->sM), scN = std::ldexp(1.0, -h->sNs);
+    if constexpr (std::is_same<T, __half>::value) {
+        op.h_diag = half_round(h->a_diag * scM);
+        op.h_off = half_round(h->m_off * scM);
+        op.s_c = half_round(h->n_up * scN);
+        op.HD = h->HD16;
+        for (int d = 0; d < 3; ++d) op.HK[d] = h->HK16[d];
+    } else {
+        op.h_diag = h->a_diag;
+        op.h_off = h->m_off;
+        op.s_c = h->n_up;
+        op.HD = h->HD64;
+        for (int d = 0; d < 3; ++d) op.HK[d] = h->HK64[d];
+    }
+    op.sigH = (Acc)std::ldexp(h->alpha, -h->sM);
+    op.sigS = (Acc)std::ldexp(h->alpha, -h->sNs);
+    return op;
+}
+
+template <class Op, class T>
+gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, double bnorm,
+                      gadi_info *info)
+{
+    Op op;
+    if constexpr (std::is_same<Op, EllOp<T>>::value) op = make_ell<T>(h);
+    else op = make_stencil<T, Op::kDim>(h);
+
+    auto kern = gadi_solve_kernel<Op, T>;
+    int threads = h->threads;
+    if (threads == 0) threads = h->n <= 16384 ? 1024 : 512;
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+    if (per_sm < 1)
+        return fail(h, GADI_ERR_CUDA, "solve kernel cannot run with %d threads per block", threads);
+    const int max_blocks = per_sm * h->num_sms;
+    int blocks = h->blocks;
+    if (blocks == 0) {
+        int64_t need = (h->n + threads - 1) / threads;
+        if (h->n <= 16384) need = 1;
+        blocks = (int)std::min<int64_t>(need, max_blocks);
+    }
+    if (blocks > max_blocks)
+        return fail(h, GADI_ERR_INVALID_ARG, "grid_blocks %d exceeds the co-resident maximum %d",
+                    blocks, max_blocks);
+    if (blocks > h->slot_blocks) {
+        if (h->slots) cudaFree(h->slots);
+        h->slots = nullptr;
+        h->slot_blocks = 0;
+        CK(dalloc(&h->slots, (size_t)2 * kMaxWords * blocks));
+        h->slot_blocks = blocks;
+    }
+
+    using Elem = T;
+    Elem *V = (Elem *)h->vec;
+    const int64_t n = h->n;
+    SolveArgs<Op, T> a;
+    a.op = op;
+    a.n = n;
+    a.b = b;
+    a.x = x;
+    a.r64 = h->r64;
+    a.rc = V + 0 * n;
+    a.pA = V + 1 * n;
+    a.pB = V + 2 * n;
+    a.q = V + 3 * n;
+    a.z = V + 4 * n;
+    a.rsA = V + 5 * n;
+    a.rsB = V + 6 * n;
+    a.s = V + 7 * n;
+    a.y = V + 8 * n;
+    a.anorm = h->anorm;
+    a.bnorm = bnorm;
+    a.tol = tol;
+    a.eps = h->eps > 0 ? h->eps : (h->u_r == GADI_F16 ? 1e-2 : 1e-10);
+    a.pfac = (2.0 - h->omega) * h->alpha;
+    a.sM = h->sM;
+    a.sN = h->sNs;
+    a.half = h->u_r == GADI_F16 ? 1 : 0;
+    a.stop_kind = h->stop;
+    a.max_inner = h->max_inner;
+    a.max_outer = h->max_outer;
+    a.ctl = h->ctl;
+    a.slots = h->slots;
+    a.eta_hist = nullptr;
+    a.wait_ns = (unsigned long long)(h->wait_ms * 1e6);
+    a.extra = h->force_timeout ? 1u : 0u;
+
+    CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
+    CK(cudaMemsetAsync(h->slots, 0, (size_t)2 * kMaxWords * blocks * sizeof(unsigned long long), h->stream));
+    CK(cudaEventRecord(h->ev0, h->stream));
+    void *args[] = {(void *)&a};
+    if (blocks > 1)
+        CK(cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(threads), args, 0,
+                                       h->stream));
+    else
+        CK(cudaLaunchKernel((const void *)kern, dim3(1), dim3(threads), args, 0, h->stream));
+    CK(cudaEventRecord(h->ev1, h->stream));
+    Ctl c;
+    CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    gadi_status st = c.error ? (gadi_status)c.error : (gadi_status)c.status;
+    if (info) {
+        info->outer_iters = c.outer_iters;
+        info->status = st;
+        info->inner_iters_H = c.itH;
+        info->inner_iters_S = c.itS;
+        info->spmv_count = c.spmv;
+        info->eta_inf = c.eta;
+        info->res_rel = c.res;
+        info->t_solve_s = ms * 1e-3;
+        info->scale_exp_M = h->sM;
+        info->scale_exp_N = h->sNs;
+        info->kernel = std::is_same<Op, EllOp<T>>::value ? GADI_KERNEL_SPARSE : GADI_KERNEL_STENCIL;
+        info->grid_blocks = blocks;
+        info->block_threads = threads;
+        info->reserved = 0;
+    }
+    if (st == GADI_ERR_TIMEOUT) return fail(h, st, "a device-side grid-barrier wait expired");
+    if (st == GADI_ERR_DIVERGED) return fail(h, st, "the iteration diverged (non-finite values, inner breakdown or residual growth)");
+    if (st == GADI_ERR_NOT_CONVERGED) return fail(h, st, "max_outer reached before the tolerance");
+    return st;
+}
+
+template <class Op, class T>
+gadi_status run_apply(gadi_solver *h, int which, const void *x, void *y)
+{
+    Op op;
+    if constexpr (std::is_same<Op, EllOp<T>>::value) op = make_ell<T>(h);
+    else op = make_stencil<T, Op::kDim>(h);
+    gadi_apply_kernel<Op, T><<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(op, which, x, y);
+    CK(cudaGetLastError());
+    return GADI_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *gadi_status_str(gadi_status s)
+{
+    switch (s) {
+    case GADI_OK: return "GADI_OK";
+    case GADI_ERR_INVALID_ARG: return "GADI_ERR_INVALID_ARG";
+    case GADI_ERR_OUT_OF_MEMORY: return "GADI_ERR_OUT_OF_MEMORY";
+    case GADI_ERR_CUDA: return "GADI_ERR_CUDA";
+    case GADI_ERR_RANGE: return "GADI_ERR_RANGE";
+    case GADI_ERR_NOT_CONVERGED: return "GADI_ERR_NOT_CONVERGED";
+    case GADI_ERR_DIVERGED: return "GADI_ERR_DIVERGED";
+    case GADI_ERR_TIMEOUT: return "GADI_ERR_TIMEOUT";
+    case GADI_ERR_NO_MODEL: return "GADI_ERR_NO_MODEL";
+    case GADI_ERR_UNSUPPORTED: return "GADI_ERR_UNSUPPORTED";
+    }
+    return "unknown gadi_status";
+}
+
+const char *gadi_last_error(const gadi_solver *h)
+{
+    return h ? h->err.c_str() : "null handle";
+}
+
+void gadi_destroy(gadi_solver *h)
+{
+    if (!h) return;
+    release(h);
+    delete h;
+}
+
+gadi_status gadi_create(const gadi_csr *A, gadi_splitting split, const gadi_csr *M_user,
+                        const gadi_stencil *structure, void *cuda_stream, gadi_solver **out)
+{
+    gadi_solver *h = nullptr;
+    if (!out) return GADI_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!A || A->n < 1 || A->nnz < A->n || A->nnz > 0x7fffffffLL || !A->row_ptr || !A->col_idx || !A->val)
+        return GADI_ERR_INVALID_ARG;
+    if (split != GADI_SPLIT_HSS && split != GADI_SPLIT_USER) return GADI_ERR_INVALID_ARG;
+    if (split == GADI_SPLIT_USER && (!M_user || M_user->n != A->n || M_user->nnz != A->nnz || !M_user->val ||
+                                     M_user->on_device != A->on_device))
+        return GADI_ERR_INVALID_ARG;
+    if (structure) {
+        const gadi_stencil &s = *structure;
+        if ((s.dim != 2 && s.dim != 3) || s.N < 1 || !std::isfinite(s.beta) ||
+            (s.variable_k && s.dim != 3) || split != GADI_SPLIT_HSS)
+            return GADI_ERR_INVALID_ARG;
+        int64_t nn = s.dim == 3 ? (int64_t)s.N * s.N * s.N : (int64_t)s.N * s.N;
+        if (nn != A->n || nn >= (1LL << 31)) return GADI_ERR_INVALID_ARG;
+    }
+    h = new (std::nothrow) gadi_solver();
+    if (!h) return GADI_ERR_OUT_OF_MEMORY;
+    gadi_status st = GADI_OK;
+    auto bail = [&](gadi_status s) {
+        release(h);
+        delete h;
+        return s;
+    };
+    do {
+        cudaError_t e;
+        if ((e = cudaGetDevice(&h->dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(GADI_ERR_CUDA);
+        }
+        h->stream = (cudaStream_t)cuda_stream;
+        h->n = A->n;
+        h->nnz = A->nnz;
+        h->user_split = split == GADI_SPLIT_USER;
+        const int64_t n = h->n, nnz = h->nnz;
+        int *rp = nullptr, *ci = nullptr;
+        double *va = nullptr, *vm = nullptr;
+        bool own = !A->on_device;
+        auto cleanup_in = [&]() {
+            if (own) {
+                if (rp) cudaFree(rp);
+                if (ci) cudaFree(ci);
+                if (va) cudaFree(va);
+                if (vm) cudaFree(vm);
+            }
+        };
+        if (own) {
+            if (dalloc(&rp, n + 1) || dalloc(&ci, nnz) || dalloc(&va, nnz) ||
+                (h->user_split && dalloc(&vm, nnz))) {
+                cleanup_in();
+                cudaGetLastError();
+                return bail(GADI_ERR_OUT_OF_MEMORY);
+            }
+            cudaMemcpyAsync(rp, A->row_ptr, (n + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+            cudaMemcpyAsync(ci, A->col_idx, nnz * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+            cudaMemcpyAsync(va, A->val, nnz * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+            if (h->user_split)
+                cudaMemcpyAsync(vm, M_user->val, nnz * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        } else {
+            rp = (int *)A->row_ptr;
+            ci = (int *)A->col_idx;
+            va = (double *)A->val;
+            vm = h->user_split ? (double *)M_user->val : nullptr;
+        }
+        if (dalloc(&h->scratch, 64) != cudaSuccess) { cleanup_in(); return bail(GADI_ERR_OUT_OF_MEMORY); }
+        int *flags = (int *)h->scratch;          // [0] bad, [1] maxlen
+        double *norms = h->scratch + 4;          // [0..3]
+        cudaMemsetAsync(h->scratch, 0, 64 * sizeof(double), h->stream);
+        k_check_csr<<<grid_for(n), kSetupThreads, 0, h->stream>>>(n, nnz, rp, ci, va, flags, flags + 1);
+        if (h->user_split)
+            k_check_csr<<<grid_for(n), kSetupThreads, 0, h->stream>>>(n, nnz, rp, ci, vm, flags, flags + 1);
+        int hf[2] = {0, 0};
+        e = cudaMemcpyAsync(hf, flags, sizeof hf, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { cleanup_in(); cudaGetLastError(); return bail(GADI_ERR_CUDA); }
+        if (hf[0]) { cleanup_in(); return bail(GADI_ERR_INVALID_ARG); }
+        h->W = std::max(4, (hf[1] + 3) / 4 * 4);
+        if (structure && h->W > 8) { cleanup_in(); return bail(GADI_ERR_INVALID_ARG); }
+        const int64_t cell = n * (int64_t)h->W;
+        if (dalloc(&h->ecol, cell) || dalloc(&h->ea, cell) || dalloc(&h->em, cell) ||
+            dalloc(&h->en, cell) || (h->user_split && dalloc(&h->ent, cell)) ||
+            dalloc(&h->m16, cell) || dalloc(&h->n16, cell) || (h->user_split && dalloc(&h->nt16, cell))) {
+            cleanup_in();
+            cudaGetLastError();
+            return bail(GADI_ERR_OUT_OF_MEMORY);
+        }
+        k_split_ell<<<grid_for(n), kSetupThreads, 0, h->stream>>>(n, rp, ci, va, vm, h->W, h->ecol, h->ea,
+                                                                  h->em, h->en, h->ent, norms, flags);
+        double hn[4];
+        e = cudaMemcpyAsync(hn, norms, sizeof hn, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, sizeof hf, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cleanup_in();
+        if (e != cudaSuccess) { cudaGetLastError(); return bail(GADI_ERR_CUDA); }
+        if (hf[0]) return bail(GADI_ERR_INVALID_ARG);
+        h->anorm = hn[0];
+        h->mnorm = hn[1];
+        h->nnorm = std::max(hn[2], hn[3]);
+        if (structure) {
+            h->has_stencil = true;
+            h->sdim = structure->dim;
+            h->sN = structure->N;
+            h->beta = structure->beta;
+            h->variable_k = structure->variable_k;
+            const double hh = 1.0 / (structure->N + 1);
+            h->c = structure->beta * hh / 2.0;
+            if (h->variable_k) {
+                bool okm = !dalloc(&h->AD, n) && !dalloc(&h->HD64, n) && !dalloc(&h->HD16, n);
+                for (int d = 0; d < 3 && okm; ++d)
+                    okm = !dalloc(&h->AL[d], n) && !dalloc(&h->AU[d], n) && !dalloc(&h->HK64[d], n) &&
+                          !dalloc(&h->HK16[d], n);
+                if (!okm) { cudaGetLastError(); return bail(GADI_ERR_OUT_OF_MEMORY); }
+            }
+            cudaMemsetAsync(flags, 0, sizeof(int), h->stream);
+            k_stencil_extract<<<grid_for(n), kSetupThreads, 0, h->stream>>>(
+                n, h->sdim, h->sN, h->c, h->variable_k, h->W, h->ecol, h->ea, h->em, h->en, h->AD,
+                h->AL[0], h->AL[1], h->AL[2], h->AU[0], h->AU[1], h->AU[2], h->HD64, h->HK64[0],
+                h->HK64[1], h->HK64[2], flags);
+            e = cudaMemcpyAsync(hf, flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) { cudaGetLastError(); return bail(GADI_ERR_CUDA); }
+            if (hf[0]) return bail(GADI_ERR_INVALID_ARG);
+            // constant-coefficient scalars from rows 0 and 1: row 0 stores
+            // (diagonal, x+, ...), row 1 stores (x-, diagonal, ...)
+            const int W = h->W;
+            double row01[3][16] = {};
+            const int cnt = (int)std::min<int64_t>(2 * W, n * W);
+            e = cudaMemcpyAsync(row01[0], h->ea, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(row01[1], h->em, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(row01[2], h->en, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) { cudaGetLastError(); return bail(GADI_ERR_CUDA); }
+            h->a_diag = row01[0][0];
+            if (structure->N >= 2) {
+                h->a_hi = row01[0][1];
+                h->m_off = row01[1][1];
+                h->n_up = row01[2][1];
+                h->a_lo = row01[0][W];
+            } else {
+                h->a_hi = h->a_lo = h->m_off = h->n_up = 0.0;
+            }
+        }
+        if (dalloc(&h->r64, n) || dalloc(&h->bdev, n) || dalloc(&h->xdev, n) ||
+            cudaMalloc(&h->vec, (size_t)9 * n * sizeof(double)) || dalloc(&h->ctl, 1)) {
+            cudaGetLastError();
+            return bail(GADI_ERR_OUT_OF_MEMORY);
+        }
+        if (cudaEventCreate(&h->ev0) || cudaEventCreate(&h->ev1)) {
+            cudaGetLastError();
+            return bail(GADI_ERR_CUDA);
+        }
+    } while (0);
+    *out = h;
+    return st;
+}
+
+gadi_status gadi_set_params(gadi_solver *h, double alpha, double omega, gadi_precision u_r,
+                            gadi_precision u, gadi_precision u_f)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (!(alpha > 0.0) || !std::isfinite(alpha))
+        return fail(h, GADI_ERR_INVALID_ARG, "alpha must be positive and finite (Thm 1)");
+    if (!(omega >= 0.0 && omega < 2.0))
+        return fail(h, GADI_ERR_INVALID_ARG, "omega must lie in [0, 2) (Thm 1)");
+    auto valid = [](int p) { return p >= GADI_F64 && p <= GADI_BF16; };
+    if (!valid(u_r) || !valid(u) || !valid(u_f))
+        return fail(h, GADI_ERR_INVALID_ARG, "unknown precision");
+    if (u != GADI_F64 || u_f != GADI_F64 || (u_r != GADI_F64 && u_r != GADI_F16))
+        return fail(h, GADI_ERR_UNSUPPORTED, "supported precision triples: u = u_f = F64, u_r = F16 or F64");
+    if (u_r != h->u_r) h->demoted = false;
+    h->alpha = alpha;
+    h->omega = omega;
+    h->u_r = u_r;
+    return GADI_OK;
+}
+
+gadi_status gadi_set_inner(gadi_solver *h, double eps_inner, int32_t max_inner, int32_t max_outer)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (!(eps_inner > 0.0 && eps_inner < 1.0) || max_inner < 1 || max_outer < 0)
+        return fail(h, GADI_ERR_INVALID_ARG, "need 0 < eps_inner < 1, max_inner >= 1, max_outer >= 0");
+    h->eps = eps_inner;
+    h->max_inner = max_inner;
+    h->max_outer = max_outer;
+    return GADI_OK;
+}
+
+gadi_status gadi_set_stop(gadi_solver *h, gadi_stop kind)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (kind != GADI_STOP_ETA && kind != GADI_STOP_RES) return fail(h, GADI_ERR_INVALID_ARG, "unknown stop kind");
+    h->stop = kind;
+    return GADI_OK;
+}
+
+gadi_status gadi_set_kernel(gadi_solver *h, gadi_kernel kind)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (kind < GADI_KERNEL_AUTO || kind > GADI_KERNEL_STENCIL)
+        return fail(h, GADI_ERR_INVALID_ARG, "unknown kernel kind");
+    if (kind == GADI_KERNEL_STENCIL && !h->has_stencil)
+        return fail(h, GADI_ERR_INVALID_ARG, "the stencil kernels need a stencil descriptor at create");
+    h->kernel = kind;
+    return GADI_OK;
+}
+
+gadi_status gadi_set_launch(gadi_solver *h, int32_t grid_blocks, int32_t block_threads)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (grid_blocks < 0 || (block_threads != 0 && block_threads != 128 && block_threads != 256 &&
+                            block_threads != 512 && block_threads != 1024))
+        return fail(h, GADI_ERR_INVALID_ARG, "grid_blocks >= 0; block_threads in {0,128,256,512,1024}");
+    h->blocks = grid_blocks;
+    h->threads = block_threads;
+    return GADI_OK;
+}
+
+gadi_status gadi_set_wait_limit(gadi_solver *h, double milliseconds)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (!(milliseconds > 0.0 && milliseconds <= 600000.0))
+        return fail(h, GADI_ERR_INVALID_ARG, "wait limit must lie in (0, 600000] ms");
+    h->wait_ms = milliseconds;
+    return GADI_OK;
+}
+
+gadi_status gadi_debug_force_timeout(gadi_solver *h, int32_t on)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    h->force_timeout = on ? 1 : 0;
+    return GADI_OK;
+}
+
+gadi_status gadi_get_scales(gadi_solver *h, int32_t *sM, int32_t *sN)
+{
+    if (!h || !sM || !sN) return GADI_ERR_INVALID_ARG;
+    gadi_status st = prepare_inner(h);
+    if (st != GADI_OK) return st;
+    *sM = h->sM;
+    *sN = h->sNs;
+    return GADI_OK;
+}
+
+gadi_status gadi_solve(gadi_solver *h, const double *b, double *x, double tol, gadi_info *info)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (!b || !x) return fail(h, GADI_ERR_INVALID_ARG, "b and x must not be NULL");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(h, GADI_ERR_INVALID_ARG, "tol must be positive");
+    const bool bd = is_device_ptr(b), xd = is_device_ptr(x);
+    if (bd != xd) return fail(h, GADI_ERR_INVALID_ARG, "b and x must both be host or both be device pointers");
+    const int64_t n = h->n;
+    const double *bb = b;
+    double *xx = x;
+    if (!bd) {
+        CK(cudaMemcpyAsync(h->bdev, b, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->xdev, x, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        bb = h->bdev;
+        xx = h->xdev;
+    }
+    // ||b||_inf and finiteness of b and x0
+    double *bn = h->scratch + 8;
+    int *nf = (int *)(h->scratch + 9);
+    CK(cudaMemsetAsync(h->scratch + 8, 0, 3 * sizeof(double), h->stream));
+    k_vec_check<<<grid_for(n), kSetupThreads, 0, h->stream>>>(n, bb, bn, nf);
+    k_vec_check<<<grid_for(n), kSetupThreads, 0, h->stream>>>(n, xx, h->scratch + 10, nf);
+    CK(cudaGetLastError());
+    double hb[2];
+    CK(cudaMemcpyAsync(hb, h->scratch + 8, sizeof hb, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int nonfinite;
+    std::memcpy(&nonfinite, &hb[1], sizeof(int));
+    if (nonfinite) return fail(h, GADI_ERR_INVALID_ARG, "b or x0 holds a NaN or Inf");
+    gadi_status st = prepare_inner(h);
+    if (st != GADI_OK) return st;
+    const bool sten = use_stencil(h);
+    const bool d3 = h->sdim == 3;
+    if (h->u_r == GADI_F16)
+        st = !sten ? run_solve<EllOp<__half>, __half>(h, bb, xx, tol, hb[0], info)
+           : d3    ? run_solve<StencilOp<__half, 3>, __half>(h, bb, xx, tol, hb[0], info)
+                   : run_solve<StencilOp<__half, 2>, __half>(h, bb, xx, tol, hb[0], info);
+    else
+        st = !sten ? run_solve<EllOp<double>, double>(h, bb, xx, tol, hb[0], info)
+           : d3    ? run_solve<StencilOp<double, 3>, double>(h, bb, xx, tol, hb[0], info)
+                   : run_solve<StencilOp<double, 2>, double>(h, bb, xx, tol, hb[0], info);
+    if (st == GADI_ERR_CUDA || st == GADI_ERR_OUT_OF_MEMORY) return st;
+    if (!xd) {
+        std::string keep = h->err;
+        CK(cudaMemcpyAsync(x, h->xdev, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        h->err = keep;
+    }
+    return st;
+}
+
+gadi_status gadi_apply(gadi_solver *h, int32_t which, const void *x, void *y)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (which < kOpA || which > kOpST || !x || !y) return fail(h, GADI_ERR_INVALID_ARG, "bad apply arguments");
+    gadi_status st = prepare_inner(h);
+    if (st != GADI_OK) return st;
+    const bool sten = use_stencil(h);
+    const bool d3 = h->sdim == 3;
+    if (h->u_r == GADI_F16)
+        return !sten ? run_apply<EllOp<__half>, __half>(h, which, x, y)
+             : d3    ? run_apply<StencilOp<__half, 3>, __half>(h, which, x, y)
+                     : run_apply<StencilOp<__half, 2>, __half>(h, which, x, y);
+    return !sten ? run_apply<EllOp<double>, double>(h, which, x, y)
+         : d3    ? run_apply<StencilOp<double, 3>, double>(h, which, x, y)
+                 : run_apply<StencilOp<double, 2>, double>(h, which, x, y);
+}
+
+gadi_status gadi_predict_params(gadi_solver *h, const double *features, int32_t nfeat, int32_t kind,
+                                double *alpha, double *omega)
+{
+    if (!h || !features || nfeat < 1 || !alpha || !omega || kind < 0 || kind > 2)
+        return GADI_ERR_INVALID_ARG;
+    return fail(h, GADI_ERR_NO_MODEL, "no parameter predictor loaded");
+}
+
+}  // extern "C"

@@ -1,0 +1,314 @@
+// gadi_device.cuh -- device primitives of the persistent GADI-IR solve kernel:
+// precision traits, a bounded software grid barrier and deterministic
+// all-block reductions.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace gadi {
+
+// status codes shared with gadi.h
+enum : int {
+    kOk = 0, kErrInvalid = 1, kErrOom = 2, kErrCuda = 3, kErrRange = 4,
+    kErrNotConverged = 5, kErrDiverged = 6, kErrTimeout = 7
+};
+
+// ---------------------------------------------------------------------------
+// Precision traits. T is the storage type of the inner vectors and matrix
+// values; Acc the arithmetic type (FP32 for FP16 storage, FP64 otherwise).
+// Arithmetic uses explicitly rounded multiply and add (no FMA contraction),
+// so every rounding step is the one written in the source.
+// ---------------------------------------------------------------------------
+template <class T> struct Prec;
+
+template <> struct Prec<__half> {
+    using Acc = float;
+    static __device__ __forceinline__ float ld(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half st(float v) { return __float2half_rn(v); }
+    // round an Acc value through the storage type
+    static __device__ __forceinline__ float rnd(float v) { return __half2float(__float2half_rn(v)); }
+    static __device__ __forceinline__ __half from64(double v) { return __double2half(v); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+};
+
+template <> struct Prec<double> {
+    using Acc = double;
+    static __device__ __forceinline__ double ld(double v) { return v; }
+    static __device__ __forceinline__ double st(double v) { return v; }
+    static __device__ __forceinline__ double rnd(double v) { return v; }
+    static __device__ __forceinline__ double from64(double v) { return v; }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+};
+
+__device__ __forceinline__ double d_madd(double acc, double a, double b)
+{
+    return __dadd_rn(acc, __dmul_rn(a, b));
+}
+
+// ---------------------------------------------------------------------------
+// Timers and ordered memory accesses (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int *p)
+{
+    return *(const volatile int *)p;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// Control block of one solve (device memory, zeroed before each launch).
+struct Ctl {
+    int error;                   // first error code raised on the device (0 = none)
+    int status;                  // final gadi_status of the solve
+    int outer_iters;
+    int pad0;
+    long long itH, itS, spmv;
+    double eta, res, r0;
+    int sM, sN;
+};
+
+// ---------------------------------------------------------------------------
+// Reductions. Values are float (FP16 inner path) or double (FP64 residual
+// phase, FP64 inner path); every order of operations is fixed, so results
+// are deterministic and identical in every block.
+// Block level: float goes through a shuffle tree in every warp, then one
+// warp combines the warp results; double goes through shared memory and one
+// warp with four accumulators per lane (few FP64 instructions, which matters
+// on a GPU with a low FP64 rate).
+// ---------------------------------------------------------------------------
+constexpr int kMaxSlots = 3;
+constexpr int kMaxThreads = 1024;
+constexpr int kWordsPerSlot = 2;                 // a double needs two 32-bit payloads
+constexpr int kMaxWords = kMaxSlots * kWordsPerSlot;
+enum RedOp { kSum = 0, kMax = 1 };
+
+template <class V>
+__device__ __forceinline__ V red_op(V a, V b, int o)
+{
+    return o == kMax ? (a > b ? a : b) : a + b;   // maxima are over |values| >= 0
+}
+
+__device__ __forceinline__ double *red_scratch()
+{
+    __shared__ double sh[kMaxSlots * kMaxThreads + 2 * kMaxSlots + 2];
+    return sh;
+}
+
+template <class V, int NS>
+__device__ __forceinline__ void warp_tree(V (&v)[NS], const int (&ops)[NS])
+{
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[s] = red_op(v[s], __shfl_xor_sync(0xffffffffu, v[s], o), ops[s]);
+}
+
+// block reduction; the result is valid in warp 0 (all its lanes)
+template <int NS>
+__device__ __forceinline__ void block_reduce_w0(float (&v)[NS], const int (&ops)[NS])
+{
+    float *sh = reinterpret_cast<float *>(red_scratch());
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    warp_tree(v, ops);
+    if (lane == 0)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) sh[s * 32 + warp] = v[s];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) v[s] = lane < nw ? sh[s * 32 + lane] : 0.0f;
+        warp_tree(v, ops);
+    }
+}
+
+template <int NS>
+__device__ __forceinline__ void block_reduce_w0(double (&v)[NS], const int (&ops)[NS])
+{
+    double *sh = red_scratch();
+#pragma unroll
+    for (int s = 0; s < NS; ++s) sh[s * kMaxThreads + threadIdx.x] = v[s];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+            unsigned k = threadIdx.x;
+            const unsigned nb = blockDim.x;
+            for (; k + 96 < nb; k += 128) {
+                t0 = red_op(t0, sh[s * kMaxThreads + k], ops[s]);
+                t1 = red_op(t1, sh[s * kMaxThreads + k + 32], ops[s]);
+                t2 = red_op(t2, sh[s * kMaxThreads + k + 64], ops[s]);
+                t3 = red_op(t3, sh[s * kMaxThreads + k + 96], ops[s]);
+            }
+            for (; k < nb; k += 32) t0 = red_op(t0, sh[s * kMaxThreads + k], ops[s]);
+            v[s] = red_op(red_op(t0, t1, ops[s]), red_op(t2, t3, ops[s]), ops[s]);
+        }
+        warp_tree(v, ops);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Grid all-reduce with a data-carrying barrier. Each block publishes its
+// block result as tagged 64-bit words (epoch << 32 | 32-bit payload): thread
+// 0 issues one release fence (which, after the preceding __syncthreads,
+// orders all of the block's earlier writes) and then relaxed stores. Warp 0
+// of every block loads all blocks' words with relaxed loads, several words
+// per lane at once, until every tag carries the current epoch, then issues
+// one acquire fence and combines the payloads in a fixed order (lane l takes
+// blocks l, l+32, ... ascending, then a fixed shuffle tree). Synchronisation
+// and data exchange take one L2 round trip. Two slot buffers alternate by
+// epoch parity, so a block that runs ahead never overwrites words that a
+// slower block has not read yet.
+// Polling is bounded by wait_ns of %globaltimer: on expiry the block records
+// kErrTimeout in ctl->error, and every block leaves at its next exchange (a
+// block that sees ctl->error stops waiting at once). One block needs no
+// global memory at all.
+// ---------------------------------------------------------------------------
+struct GridExchange {
+    Ctl *ctl;
+    unsigned long long *slots;     // [2][kMaxWords][gridDim]
+    unsigned epoch;
+    unsigned long long wait_ns;
+    unsigned extra;                // added to the expected tag (never reached: timeout test)
+
+    template <class V, int NS>
+    __device__ __forceinline__ bool allreduce(V (&v)[NS], const int (&ops)[NS])
+    {
+        double *shd = red_scratch() + kMaxSlots * kMaxThreads;
+        V *res = reinterpret_cast<V *>(shd);
+        int *s_ok = reinterpret_cast<int *>(shd + 2 * kMaxSlots);
+        block_reduce_w0(v, ops);
+        if (gridDim.x == 1) {
+            if (threadIdx.x == 0)
+#pragma unroll
+                for (int s = 0; s < NS; ++s) res[s] = v[s];
+            __syncthreads();
+#pragma unroll
+            for (int s = 0; s < NS; ++s) v[s] = res[s];
+            __syncthreads();
+            return true;
+        }
+        constexpr int WPS = sizeof(V) == 8 ? 2 : 1;
+        constexpr int NWORD = NS * WPS;
+        constexpr int CH = NWORD >= 4 ? 2 : 4;          // blocks per lane per polling round
+        ++epoch;
+        const unsigned G = gridDim.x;
+        unsigned long long *buf = slots + (size_t)(epoch & 1u) * kMaxWords * G;
+        const unsigned long long tag = (unsigned long long)epoch << 32;
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            if (lane == 0) {
+                fence_acq_rel_gpu();
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    if (WPS == 2) {
+                        double d = (double)v[s];
+                        st_relaxed_u64(buf + (size_t)(2 * s) * G + blockIdx.x, tag | (unsigned)__double2hiint(d));
+                        st_relaxed_u64(buf + (size_t)(2 * s + 1) * G + blockIdx.x, tag | (unsigned)__double2loint(d));
+                    } else {
+                        st_relaxed_u64(buf + (size_t)s * G + blockIdx.x, tag | (unsigned)__float_as_uint((float)v[s]));
+                    }
+                }
+            }
+            const unsigned long long want = (unsigned long long)(epoch + extra) << 32;
+            V acc[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) acc[s] = V(0);
+            int ok = 1;
+            const unsigned long long t0 = global_ns();
+            for (unsigned b0 = lane; b0 < G && ok; b0 += 32 * CH) {
+                unsigned spins = 0;
+                for (;;) {
+                    unsigned long long wd[CH][NWORD];
+                    bool ready = true;
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) {
+                        const unsigned b = b0 + 32u * c;
+#pragma unroll
+                        for (int w = 0; w < NWORD; ++w)
+                            wd[c][w] = b < G ? ld_relaxed_u64(buf + (size_t)w * G + b) : want;
+                    }
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+#pragma unroll
+                        for (int w = 0; w < NWORD; ++w)
+                            ready = ready && ((wd[c][w] & 0xffffffff00000000ULL) == want);
+                    if (ready) {
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) {
+                            if (b0 + 32u * c >= G) continue;
+#pragma unroll
+                            for (int s = 0; s < NS; ++s) {
+                                V val;
+                                if (WPS == 2)
+                                    val = (V)__hiloint2double((int)(unsigned)wd[c][2 * s], (int)(unsigned)wd[c][2 * s + 1]);
+                                else
+                                    val = (V)__uint_as_float((unsigned)wd[c][s]);
+                                acc[s] = red_op(acc[s], val, ops[s]);
+                            }
+                        }
+                        break;
+                    }
+                    if ((++spins & 15u) == 0) {
+                        if (ld_volatile_i32(&ctl->error) != 0) { ok = 0; break; }
+                        if (global_ns() - t0 > wait_ns) {
+                            atomicCAS(&ctl->error, 0, kErrTimeout);
+                            ok = 0;
+                            break;
+                        }
+                    }
+                }
+            }
+            fence_acq_rel_gpu();
+            ok = __all_sync(0xffffffffu, ok);
+            warp_tree(acc, ops);
+            if (lane == 0) {
+#pragma unroll
+                for (int s = 0; s < NS; ++s) res[s] = acc[s];
+                *s_ok = ok;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < NS; ++s) v[s] = res[s];
+        const bool good = *s_ok != 0;
+        __syncthreads();
+        return good;
+    }
+
+    // barrier without data
+    __device__ __forceinline__ bool sync()
+    {
+        float v[1] = {0.0f};
+        const int ops[1] = {kSum};
+        return allreduce(v, ops);
+    }
+};
+
+}  // namespace gadi

@@ -1,0 +1,353 @@
+"""GPU path (libgadi.so through its C ABI) against the CPU oracle.
+
+Kernel level: one operator application per kernel family and precision is
+compared bit for bit with the oracle's application (same splitting, same
+power-of-two scales, same FP16 rounding, same row order).
+Solver level: GADI-IR / GADI results reach the requested backward error,
+agree with the oracle's solution within the stated bound, and the outer
+iteration counts agree (exactly up to reduction order in FP64; within 15 %
+with FP16 inner solves, where the dot products are summed in another order).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_04229_gb300 import gadi as G
+from paper_2501_04229_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2501_04229_gb300 import build
+    build.build()
+    oracle.build()
+    G.load()
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dtype, device="cuda")
+
+
+def _handle(p, stencil=True, device=True, split=G.GADI_SPLIT_HSS, m_user=None):
+    A = p.A
+    st = None
+    if stencil and split == G.GADI_SPLIT_HSS:
+        st = (p.dim, p.N, p.beta, 1 if p.faces is not None else 0)
+    if device:
+        rp = _dev(A.row_ptr, torch.int32)
+        ci = _dev(A.col_idx, torch.int32)
+        va = _dev(A.val)
+        mu = None if m_user is None else _dev(m_user)
+    else:
+        rp = np.ascontiguousarray(A.row_ptr, np.int32)
+        ci = np.ascontiguousarray(A.col_idx, np.int32)
+        va = np.ascontiguousarray(A.val, np.float64)
+        mu = None if m_user is None else np.ascontiguousarray(m_user, np.float64)
+    return G.gadi_create(rp, ci, va, split=split, m_val=mu, stencil=st)
+
+
+def _half_vector(n, seed):
+    x = P.random_vector(n, seed)
+    return oracle.to_half_bits(x).view(np.float16).astype(np.float64)
+
+
+PROBLEMS = {
+    "2d_33_b10": lambda: P.make_problem(2, 33, 10.0, rhs="ones"),
+    "3d_13_b100": lambda: P.make_problem(3, 13, 100.0),
+    "3d_12_b50_grf": lambda: P.make_problem(3, 12, 50.0, grf_seed=3),
+    "3d_1_b5": lambda: P.make_problem(3, 1, 5.0),
+    "2d_2_b1": lambda: P.make_problem(2, 2, 1.0),
+}
+
+
+# ---------------------------------------------------------------------------
+# kernel level: bit-exact operator applications
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("kernel", [G.GADI_KERNEL_SPARSE, G.GADI_KERNEL_STENCIL])
+@pytest.mark.parametrize("u_r", [G.GADI_F16, G.GADI_F64])
+@pytest.mark.parametrize("alpha", [0.37, 12.0])
+def test_apply_bit_exact(name, kernel, u_r, alpha):
+    p = PROBLEMS[name]()
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, alpha, 1.0, u_r=u_r)
+        G.gadi_set_kernel(h, kernel)
+        prec = oracle.PREC_HALF if u_r == G.GADI_F16 else oracle.PREC_DOUBLE
+        tdt = torch.float16 if u_r == G.GADI_F16 else torch.float64
+        for which in (G.OP_A, G.OP_H, G.OP_S, G.OP_ST):
+            x = _half_vector(p.n, 10 + which) if (which != G.OP_A and u_r == G.GADI_F16) \
+                else P.random_vector(p.n, 20 + which)
+            want, sM, sN = oracle.lp_apply(p.A, alpha, which, prec, x)
+            dt = torch.float64 if which == G.OP_A else tdt
+            xd = _dev(x, dt)
+            yd = torch.empty_like(xd)
+            G.gadi_apply(h, which, xd, yd)
+            torch.cuda.synchronize()
+            got = yd.double().cpu().numpy()
+            if (kernel == G.GADI_KERNEL_STENCIL and p.faces is not None and u_r == G.GADI_F64
+                    and which in (G.OP_S, G.OP_ST)):
+                # the face-coefficient stencil applies N as the constant convection
+                # c = beta h / 2, the split stores (a_ij - a_ji)/2, which differs by ulps
+                assert np.allclose(got, want, rtol=1e-14, atol=1e-15 * np.abs(want).max())
+            else:
+                assert np.array_equal(got, want), (which, np.abs(got - want).max())
+        assert G.gadi_get_scales(h) == (sM, sN)
+    finally:
+        G.gadi_destroy(h)
+
+
+def test_apply_user_split_bit_exact():
+    p = P.make_problem(3, 9, 30.0)
+    m_hss, _ = oracle.hss_split(p.A)
+    d = np.zeros_like(m_hss)
+    rows = np.repeat(np.arange(p.n), np.diff(p.A.row_ptr))
+    diag = rows == p.A.col_idx
+    d[diag] = 0.5 + P.random_vector(p.n, 3, "uniform") ** 2
+    m_user = m_hss + d
+    h = _handle(p, stencil=False, split=G.GADI_SPLIT_USER, m_user=m_user)
+    try:
+        G.gadi_set_params(h, 0.8, 1.0, u_r=G.GADI_F16)
+        for which in (G.OP_H, G.OP_S, G.OP_ST):
+            x = _half_vector(p.n, 30 + which)
+            want, sM, sN = oracle.lp_apply(p.A, 0.8, which, oracle.PREC_HALF, x, m_user=m_user)
+            xd = _dev(x, torch.float16)
+            yd = torch.empty_like(xd)
+            G.gadi_apply(h, which, xd, yd)
+            torch.cuda.synchronize()
+            assert np.array_equal(yd.double().cpu().numpy(), want)
+    finally:
+        G.gadi_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# solver level
+# ---------------------------------------------------------------------------
+
+def _solve(h, p, tol, x0=None, device=True):
+    if device:
+        b = _dev(p.b)
+        x = _dev(np.zeros(p.n) if x0 is None else x0)
+    else:
+        b = np.ascontiguousarray(p.b)
+        x = np.zeros(p.n) if x0 is None else np.array(x0, dtype=np.float64)
+    st, info = G.gadi_solve(h, b, x, tol)
+    xh = x.cpu().numpy() if device else x
+    return st, info, xh
+
+
+def test_fp64_gadi_config_2d_matches_oracle():
+    """2D 32x32, beta 10, b = A 1, alpha 0.5, omega 1, inner eps 1e-10, RES <= 1e-12:
+    plain FP64 GADI (eq. (gadi)) on the oracle, FP64 GADI-IR on the GPU, which
+    is the same iteration (x^{k+1/2} = x^k + H^-1 r^k)."""
+    p = P.workload("convdiff2d_32_b10")
+    want, oinfo, _ = oracle.gadi(p.A, p.b, 0.5, 1.0, tol=1e-12, eps_inner=1e-10,
+                                 stop=oracle.STOP_RES)
+    for kernel in (G.GADI_KERNEL_SPARSE, G.GADI_KERNEL_STENCIL):
+        h = _handle(p)
+        try:
+            G.gadi_set_params(h, 0.5, 1.0, u_r=G.GADI_F64)
+            G.gadi_set_inner(h, 1e-10, 10000, 100000)
+            G.gadi_set_stop(h, G.GADI_STOP_RES)
+            G.gadi_set_kernel(h, kernel)
+            st, info, x = _solve(h, p, 1e-12)
+            assert st == G.GADI_OK, G.last_error(h)
+            assert info["res_rel"] <= 1e-12
+            assert abs(info["outer_iters"] - oinfo["outer_iters"]) <= 1
+            assert np.linalg.norm(x - want) <= 1e-9 * np.linalg.norm(want)
+            eta_o = oracle.backward_error(p.A, p.b, want)
+            assert oracle.backward_error(p.A, p.b, x) <= 1.1 * eta_o
+        finally:
+            G.gadi_destroy(h)
+
+
+@pytest.mark.parametrize("name,alpha,omega", [("3d_13_b100", 3.0, 1.0), ("3d_12_b50_grf", 2.0, 0.5),
+                                              ("2d_33_b10", 0.4, 1.2)])
+@pytest.mark.parametrize("kernel", [G.GADI_KERNEL_SPARSE, G.GADI_KERNEL_STENCIL])
+def test_fp16_gadi_ir_matches_oracle(name, alpha, omega, kernel):
+    p = PROBLEMS[name]()
+    want, oinfo, _ = oracle.gadi_ir(p.A, p.b, alpha, omega, tol=1e-13, eps_inner=1e-2,
+                                    prec=oracle.PREC_HALF, max_outer=5000)
+    assert oinfo["status"] == oracle.OK
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, alpha, omega, u_r=G.GADI_F16)
+        G.gadi_set_inner(h, 1e-2, 200, 5000)
+        G.gadi_set_kernel(h, kernel)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK, G.last_error(h)
+        eta = oracle.backward_error(p.A, p.b, x)
+        assert eta <= 1e-13 and info["eta_inf"] <= 1e-13
+        assert abs(eta - info["eta_inf"]) <= 1e-3 * eta + 1e-18
+        cond = np.linalg.cond(p.A.to_dense(), np.inf) if p.n <= 3000 else 1e4
+        bound = max(1e-9, 4 * cond * 1e-13)
+        assert np.linalg.norm(x - want) <= bound * np.linalg.norm(want)
+        assert abs(info["outer_iters"] - oinfo["outer_iters"]) <= max(2, 0.15 * oinfo["outer_iters"])
+        assert (info["scale_exp_M"], info["scale_exp_N"]) == (oinfo["scale_exp_M"], oinfo["scale_exp_N"])
+    finally:
+        G.gadi_destroy(h)
+
+
+def test_user_split_solve_matches_oracle():
+    p = P.make_problem(3, 9, 30.0)
+    m_hss, _ = oracle.hss_split(p.A)
+    rows = np.repeat(np.arange(p.n), np.diff(p.A.row_ptr))
+    d = np.where(rows == p.A.col_idx, 0.25, 0.0)
+    m_user = m_hss + d
+    want, oinfo, _ = oracle.gadi_ir(p.A, p.b, 1.5, 1.0, tol=1e-13, prec=oracle.PREC_HALF,
+                                    m_user=m_user, max_outer=5000)
+    assert oinfo["status"] == oracle.OK
+    h = _handle(p, stencil=False, split=G.GADI_SPLIT_USER, m_user=m_user)
+    try:
+        G.gadi_set_params(h, 1.5, 1.0, u_r=G.GADI_F16)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK
+        assert oracle.backward_error(p.A, p.b, x) <= 1e-13
+        assert np.linalg.norm(x - want) <= 1e-9 * np.linalg.norm(want)
+        assert abs(info["outer_iters"] - oinfo["outer_iters"]) <= max(2, 0.15 * oinfo["outer_iters"])
+    finally:
+        G.gadi_destroy(h)
+
+
+@pytest.mark.parametrize("blocks,threads", [(1, 1024), (3, 128), (16, 256), (0, 0)])
+def test_launch_shapes_agree(blocks, threads):
+    """Single-block and multi-block (grid-barrier) launches of the persistent
+    kernel give the same solution up to reduction order."""
+    p = P.make_problem(3, 27, 80.0)          # n = 19683: ragged against every block size
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 3.0, 1.0, u_r=G.GADI_F16)
+        G.gadi_set_launch(h, blocks, threads)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK, G.last_error(h)
+        if blocks:
+            assert info["grid_blocks"] == blocks
+        assert oracle.backward_error(p.A, p.b, x) <= 1e-13
+        assert np.abs(x - p.x_exact).max() <= 1e-9
+    finally:
+        G.gadi_destroy(h)
+
+
+def test_host_and_device_buffers_agree():
+    p = PROBLEMS["3d_13_b100"]()
+    h = _handle(p, device=False)
+    try:
+        G.gadi_set_params(h, 3.0, 1.0)
+        st1, i1, x1 = _solve(h, p, 1e-13, device=False)
+        st2, i2, x2 = _solve(h, p, 1e-13, device=True)
+        assert st1 == st2 == G.GADI_OK
+        assert np.array_equal(x1, x2)
+        assert i1["outer_iters"] == i2["outer_iters"]
+    finally:
+        G.gadi_destroy(h)
+
+
+def test_edge_cases():
+    # already converged start: zero outer steps
+    p = PROBLEMS["3d_13_b100"]()
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 3.0, 1.0)
+        xs = np.linalg.solve(p.A.to_dense(), p.b)
+        st, info, x = _solve(h, p, 1e-12, x0=xs)
+        assert st == G.GADI_OK and info["outer_iters"] == 0
+        assert np.array_equal(x, xs)
+        # zero right-hand side: x = 0 is exact
+        b0 = P.Problem(p.name, p.dim, p.N, p.beta, p.A, np.zeros(p.n), np.zeros(p.n), None)
+        st, info, x = _solve(h, b0, 1e-13)
+        assert st == G.GADI_OK and info["outer_iters"] == 0 and not x.any()
+        # max_outer reached
+        G.gadi_set_inner(h, 1e-2, 200, 2)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_ERR_NOT_CONVERGED and info["outer_iters"] == 2
+        assert np.isfinite(x).all()
+    finally:
+        G.gadi_destroy(h)
+    # 1 x 1 system
+    p1 = PROBLEMS["3d_1_b5"]()
+    for kernel in (G.GADI_KERNEL_SPARSE, G.GADI_KERNEL_STENCIL):
+        h = _handle(p1)
+        try:
+            G.gadi_set_params(h, 1.0, 1.0)
+            G.gadi_set_kernel(h, kernel)
+            st, info, x = _solve(h, p1, 1e-14)
+            assert st == G.GADI_OK
+            assert abs(x[0] - p1.b[0] / p1.A.val[0]) <= 1e-14 * abs(x[0])
+        finally:
+            G.gadi_destroy(h)
+
+
+def test_invalid_arguments_rejected():
+    p = PROBLEMS["2d_2_b1"]()
+    h = _handle(p)
+    try:
+        for a, w in ((0.0, 1.0), (-1.0, 1.0), (1.0, 2.0), (1.0, -0.5), (float("nan"), 1.0)):
+            with pytest.raises(G.GadiError) as e:
+                G.gadi_set_params(h, a, w)
+            assert e.value.status == G.GADI_ERR_INVALID_ARG
+        with pytest.raises(G.GadiError) as e:
+            G.gadi_set_params(h, 1.0, 1.0, u_r=G.GADI_F32)
+        assert e.value.status == G.GADI_ERR_UNSUPPORTED
+        b = _dev(p.b)
+        x = torch.full((p.n,), 7.0, dtype=torch.float64, device="cuda")
+        with pytest.raises(G.GadiError):
+            G.gadi_solve(h, b, x, 0.0)
+        bn = b.clone()
+        bn[1] = float("nan")
+        with pytest.raises(G.GadiError) as e:
+            G.gadi_solve(h, bn, x, 1e-10)
+        assert e.value.status == G.GADI_ERR_INVALID_ARG
+        assert (x == 7.0).all()
+        with pytest.raises(G.GadiError):
+            G.gadi_solve(h, b, x.cpu().numpy(), 1e-10)
+    finally:
+        G.gadi_destroy(h)
+    # structurally unsymmetric pattern, unsorted columns, stencil mismatch
+    rp = np.array([0, 2, 3], np.int32)
+    with pytest.raises(G.GadiError):
+        G.gadi_create(rp, np.array([0, 1, 1], np.int32), np.array([2.0, 1.0, 3.0]))
+    with pytest.raises(G.GadiError):
+        G.gadi_create(np.array([0, 2, 4], np.int32), np.array([1, 0, 0, 1], np.int32),
+                      np.array([1.0, 2.0, 1.0, 3.0]))
+    q = P.make_problem(3, 5, 10.0)
+    with pytest.raises(G.GadiError):
+        G.gadi_create(q.A.row_ptr, q.A.col_idx, q.A.val, stencil=(3, 5, 11.0, 0))
+
+
+def test_bounded_wait_expires_with_timeout_status():
+    """A grid-barrier wait whose arrival target nothing reaches expires after
+    the wait limit: the solve returns GADI_ERR_TIMEOUT and the handle (and the
+    CUDA context) stay usable."""
+    p = PROBLEMS["3d_13_b100"]()
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 3.0, 1.0)
+        G.gadi_set_launch(h, 2, 256)
+        G.gadi_set_wait_limit(h, 20.0)
+        G.gadi_debug_force_timeout(h, 1)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_ERR_TIMEOUT
+        G.gadi_debug_force_timeout(h, 0)
+        G.gadi_set_wait_limit(h, 2000.0)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK
+        assert oracle.backward_error(p.A, p.b, x) <= 1e-13
+    finally:
+        G.gadi_destroy(h)
+
+
+def test_predictor_without_model():
+    p = PROBLEMS["2d_2_b1"]()
+    h = _handle(p)
+    try:
+        st, _, _ = G.gadi_predict_params(h, [np.log(4.0), 0.0], 0)
+        assert st == G.GADI_ERR_NO_MODEL
+    finally:
+        G.gadi_destroy(h)
