@@ -28,9 +28,13 @@
  *     FP64 update scalar. The "naive" half mode instead rounds alpha into the
  *     FP16 diagonal and scales nothing, for the paper's unscaled behaviour.
  *
+ * Rounding: FP64 products are fused with their sum (C99 fma, one rounding per
+ * term), the paper fixing only the precision (u_f = u = double); FP32
+ * arithmetic of the low-precision modes rounds every product and sum
+ * separately. Compile with -ffp-contract=off so that nothing else is fused.
  * Determinism: dot products are summed in fixed blocks of OR_BLK elements and
  * the block sums are added in order, so results do not depend on the number
- * of OpenMP threads. Compile with -ffp-contract=off.
+ * of OpenMP threads.
  */
 #include <math.h>
 #include <stdint.h>
@@ -99,7 +103,7 @@ static double dot64(int64_t n, const double *a, const double *b)
     for (int64_t k = 0; k < nb; ++k) {
         int64_t lo = k * OR_BLK, hi = lo + OR_BLK < n ? lo + OR_BLK : n;
         double s = 0.0;
-        for (int64_t i = lo; i < hi; ++i) s += a[i] * b[i];
+        for (int64_t i = lo; i < hi; ++i) s = fma(a[i], b[i], s);
         part[k] = s;
     }
     double s = 0.0;
@@ -126,7 +130,7 @@ void or_spmv_shift(int64_t n, const int32_t *rp, const int32_t *ci, const double
     #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         double s = sigma * x[i];
-        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * x[ci[k]];
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = fma(v[k], x[ci[k]], s);
         y[i] = s;
     }
 }
@@ -138,7 +142,7 @@ void or_residual(int64_t n, const int32_t *rp, const int32_t *ci, const double *
     #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
-        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s += a[k] * x[ci[k]];
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = fma(a[k], x[ci[k]], s);
         r[i] = b[i] - s;
     }
 }
@@ -254,13 +258,13 @@ int64_t or_cg(int64_t n, const int32_t *rp, const int32_t *ci, const double *m, 
             if (!(pq > 0.0) || !isfinite(pq)) { it = -1; break; }
             double a = rr / pq;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-            for (int64_t i = 0; i < n; ++i) { v[i] += a * p[i]; r[i] -= a * q[i]; }
+            for (int64_t i = 0; i < n; ++i) { v[i] = fma(a, p[i], v[i]); r[i] = fma(-a, q[i], r[i]); }
             double rrn = dot64(n, r, r);
             if (!isfinite(rrn)) { it = -1; break; }
             if (rrn <= eps * eps * rr0) break;
             double beta = rrn / rr;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-            for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+            for (int64_t i = 0; i < n; ++i) p[i] = fma(beta, p[i], r[i]);
             rr = rrn;
         }
     }
@@ -295,7 +299,7 @@ int64_t or_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const double *v
             if (!(qq > 0.0) || !isfinite(qq)) { it = -1; break; }
             double a = g / qq;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-            for (int64_t i = 0; i < n; ++i) { v[i] += a * p[i]; r[i] -= a * q[i]; }
+            for (int64_t i = 0; i < n; ++i) { v[i] = fma(a, p[i], v[i]); r[i] = fma(-a, q[i], r[i]); }
             double rr = dot64(n, r, r);
             if (!isfinite(rr)) { it = -1; break; }
             if (rr <= eps * eps * rr0) break;
@@ -303,7 +307,7 @@ int64_t or_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const double *v
             double gn = dot64(n, s, s);
             double beta = gn / g;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-            for (int64_t i = 0; i < n; ++i) p[i] = s[i] + beta * p[i];
+            for (int64_t i = 0; i < n; ++i) p[i] = fma(beta, p[i], s[i]);
             g = gn;
         }
     }
@@ -548,7 +552,7 @@ int or_gadi(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
         /* second half step: rhs = (N - (1-w) a I) x + (2-w) a xh, solve (aI + N) xn = rhs from x */
         or_spmv_shift(n, rp, ci, nv, -(1.0 - om) * al, x, t);
         #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-        for (int64_t i = 0; i < n; ++i) { rhs[i] = t[i] + (2.0 - om) * al * xh[i]; xn[i] = x[i]; }
+        for (int64_t i = 0; i < n; ++i) { rhs[i] = fma((2.0 - om) * al, xh[i], t[i]); xn[i] = x[i]; }
         int64_t is = or_cgnr(n, rp, ci, nv, rpt, cit, nvt, al, rhs, xn, P->eps_inner, P->max_inner);
         if (is < 0) { status = OR_DIVERGED; break; }
         memcpy(x, xn, szv);
@@ -702,7 +706,7 @@ int or_gadi_ir_split(int64_t n, const int32_t *rp, const int32_t *ci, const doub
             if (is < 0) { status = OR_DIVERGED; break; }
             /* step 4 in u = FP64 */
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-            for (int64_t i = 0; i < n; ++i) x[i] += upd * (double)yf[i];
+            for (int64_t i = 0; i < n; ++i) x[i] = fma(upd, (double)yf[i], x[i]);
         }
         info->inner_iters_H += ih;
         info->inner_iters_S += is;

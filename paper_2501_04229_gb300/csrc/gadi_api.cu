@@ -276,8 +276,8 @@ struct gadi_solver {
     // work
     double *bdev = nullptr, *xdev = nullptr, *r64 = nullptr;
     void *vec = nullptr;      // 9 vectors of n elements of the inner type (sized for FP64)
-    unsigned long long *slots = nullptr;
-    int slot_blocks = 0;
+    double *part = nullptr;
+    int part_blocks = 0;
     Ctl *ctl = nullptr;
     double *scratch = nullptr;   // small device scratch (norms, flags)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -321,7 +321,7 @@ void release(gadi_solver *h)
     void *ptrs[] = {h->ecol, h->ea, h->em, h->en, h->ent, h->m16, h->n16, h->nt16, h->AD,
                     h->AL[0], h->AL[1], h->AL[2], h->AU[0], h->AU[1], h->AU[2], h->HD64,
                     h->HK64[0], h->HK64[1], h->HK64[2], h->HD16, h->HK16[0], h->HK16[1],
-                    h->HK16[2], h->bdev, h->xdev, h->r64, h->vec, h->slots, h->ctl, h->scratch};
+                    h->HK16[2], h->bdev, h->xdev, h->r64, h->vec, h->part, h->ctl, h->scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -422,11 +422,11 @@ float half_round(double v)
     return __half2float(__double2half(v));
 }
 
-template <class T, int DIM>
-StencilOp<T, DIM> make_stencil(const gadi_solver *h)
+template <class T, int DIM, int R>
+StencilOp<T, DIM, R> make_stencil(const gadi_solver *h)
 {
     using Acc = typename Prec<T>::Acc;
-    StencilOp<T, DIM> op{};
+    StencilOp<T, DIM, R> op{};
     op.dim = h->sdim;
     op.N = h->sN;
     op.n = h->n;
@@ -463,11 +463,21 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
 {
     Op op;
     if constexpr (std::is_same<Op, EllOp<T>>::value) op = make_ell<T>(h);
-    else op = make_stencil<T, Op::kDim>(h);
+    else op = make_stencil<T, Op::kDim, Op::R>(h);
+    const int64_t nitems = h->n / Op::R;
 
     auto kern = gadi_solve_kernel<Op, T>;
     int threads = h->threads;
-    if (threads == 0) threads = h->n <= 16384 ? 1024 : 512;
+    if (threads == 0) {
+        // enough threads for one item each on every SM, between 128 and 1024
+        const int64_t per_sm = (nitems + h->num_sms - 1) / h->num_sms;
+        threads = 128;
+        while (threads < max_threads<Op>() && threads < per_sm) threads *= 2;
+        if (nitems <= 16384) threads = max_threads<Op>();
+    }
+    if (threads > max_threads<Op>())
+        return fail(h, GADI_ERR_INVALID_ARG, "block_threads %d exceeds %d for this kernel", threads,
+                    max_threads<Op>());
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
     if (per_sm < 1)
@@ -475,39 +485,31 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     const int max_blocks = per_sm * h->num_sms;
     int blocks = h->blocks;
     if (blocks == 0) {
-        int64_t need = (h->n + threads - 1) / threads;
-        if (h->n <= 16384) need = 1;
+        int64_t need = (nitems + threads - 1) / threads;
+        if (nitems <= 16384) need = 1;
         blocks = (int)std::min<int64_t>(need, max_blocks);
     }
     if (blocks > max_blocks)
         return fail(h, GADI_ERR_INVALID_ARG, "grid_blocks %d exceeds the co-resident maximum %d",
                     blocks, max_blocks);
-    if (blocks > h->slot_blocks) {
-        if (h->slots) cudaFree(h->slots);
-        h->slots = nullptr;
-        h->slot_blocks = 0;
-        CK(dalloc(&h->slots, (size_t)2 * kMaxWords * blocks));
-        h->slot_blocks = blocks;
+    if (blocks > h->part_blocks) {
+        if (h->part) cudaFree(h->part);
+        h->part = nullptr;
+        h->part_blocks = 0;
+        CK(dalloc(&h->part, (size_t)2 * kMaxSlots * blocks));
+        h->part_blocks = blocks;
     }
 
-    using Elem = T;
-    Elem *V = (Elem *)h->vec;
+    T *V = (T *)h->vec;
     const int64_t n = h->n;
     SolveArgs<Op, T> a;
     a.op = op;
     a.n = n;
+    a.nitems = nitems;
     a.b = b;
     a.x = x;
     a.r64 = h->r64;
-    a.rc = V + 0 * n;
-    a.pA = V + 1 * n;
-    a.pB = V + 2 * n;
-    a.q = V + 3 * n;
-    a.z = V + 4 * n;
-    a.rsA = V + 5 * n;
-    a.rsB = V + 6 * n;
-    a.s = V + 7 * n;
-    a.y = V + 8 * n;
+    for (int j = 0; j < 9; ++j) a.v[j] = V + j * n;
     a.anorm = h->anorm;
     a.bnorm = bnorm;
     a.tol = tol;
@@ -520,13 +522,12 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     a.max_inner = h->max_inner;
     a.max_outer = h->max_outer;
     a.ctl = h->ctl;
-    a.slots = h->slots;
+    a.part = h->part;
     a.eta_hist = nullptr;
     a.wait_ns = (unsigned long long)(h->wait_ms * 1e6);
     a.extra = h->force_timeout ? 1u : 0u;
 
     CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
-    CK(cudaMemsetAsync(h->slots, 0, (size_t)2 * kMaxWords * blocks * sizeof(unsigned long long), h->stream));
     CK(cudaEventRecord(h->ev0, h->stream));
     void *args[] = {(void *)&a};
     if (blocks > 1)
@@ -568,10 +569,36 @@ gadi_status run_apply(gadi_solver *h, int which, const void *x, void *y)
 {
     Op op;
     if constexpr (std::is_same<Op, EllOp<T>>::value) op = make_ell<T>(h);
-    else op = make_stencil<T, Op::kDim>(h);
-    gadi_apply_kernel<Op, T><<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(op, which, x, y);
+    else op = make_stencil<T, Op::kDim, Op::R>(h);
+    const int64_t nitems = h->n / Op::R;
+    gadi_apply_kernel<Op, T><<<grid_for(nitems), kSetupThreads, 0, h->stream>>>(op, nitems, which, x, y);
     CK(cudaGetLastError());
     return GADI_OK;
+}
+
+template <class X>
+struct Tag {
+    using type = X;
+};
+
+// call fn(Tag<Op>, Tag<T>) with the operator family and inner type in use:
+// the sparse operator, or the stencil for dim 2/3 with 8-row items when
+// the grid side is a multiple of 8
+template <class T, class Fn>
+gadi_status dispatch_op(const gadi_solver *h, Fn &&fn)
+{
+    if (!use_stencil(h)) return fn(Tag<EllOp<T>>{}, Tag<T>{});
+    const bool v8 = h->sN % 8 == 0;
+    if (h->sdim == 3)
+        return v8 ? fn(Tag<StencilOp<T, 3, 8>>{}, Tag<T>{}) : fn(Tag<StencilOp<T, 3, 1>>{}, Tag<T>{});
+    return v8 ? fn(Tag<StencilOp<T, 2, 8>>{}, Tag<T>{}) : fn(Tag<StencilOp<T, 2, 1>>{}, Tag<T>{});
+}
+
+template <class Fn>
+gadi_status dispatch(const gadi_solver *h, Fn &&fn)
+{
+    if (h->u_r == GADI_F16) return dispatch_op<__half>(h, fn);
+    return dispatch_op<double>(h, fn);
 }
 
 }  // namespace
@@ -889,16 +916,11 @@ gadi_status gadi_solve(gadi_solver *h, const double *b, double *x, double tol, g
     if (nonfinite) return fail(h, GADI_ERR_INVALID_ARG, "b or x0 holds a NaN or Inf");
     gadi_status st = prepare_inner(h);
     if (st != GADI_OK) return st;
-    const bool sten = use_stencil(h);
-    const bool d3 = h->sdim == 3;
-    if (h->u_r == GADI_F16)
-        st = !sten ? run_solve<EllOp<__half>, __half>(h, bb, xx, tol, hb[0], info)
-           : d3    ? run_solve<StencilOp<__half, 3>, __half>(h, bb, xx, tol, hb[0], info)
-                   : run_solve<StencilOp<__half, 2>, __half>(h, bb, xx, tol, hb[0], info);
-    else
-        st = !sten ? run_solve<EllOp<double>, double>(h, bb, xx, tol, hb[0], info)
-           : d3    ? run_solve<StencilOp<double, 3>, double>(h, bb, xx, tol, hb[0], info)
-                   : run_solve<StencilOp<double, 2>, double>(h, bb, xx, tol, hb[0], info);
+    st = dispatch(h, [&](auto opk, auto tk) {
+        using Op = typename decltype(opk)::type;
+        using T = typename decltype(tk)::type;
+        return run_solve<Op, T>(h, bb, xx, tol, hb[0], info);
+    });
     if (st == GADI_ERR_CUDA || st == GADI_ERR_OUT_OF_MEMORY) return st;
     if (!xd) {
         std::string keep = h->err;
@@ -915,15 +937,11 @@ gadi_status gadi_apply(gadi_solver *h, int32_t which, const void *x, void *y)
     if (which < kOpA || which > kOpST || !x || !y) return fail(h, GADI_ERR_INVALID_ARG, "bad apply arguments");
     gadi_status st = prepare_inner(h);
     if (st != GADI_OK) return st;
-    const bool sten = use_stencil(h);
-    const bool d3 = h->sdim == 3;
-    if (h->u_r == GADI_F16)
-        return !sten ? run_apply<EllOp<__half>, __half>(h, which, x, y)
-             : d3    ? run_apply<StencilOp<__half, 3>, __half>(h, which, x, y)
-                     : run_apply<StencilOp<__half, 2>, __half>(h, which, x, y);
-    return !sten ? run_apply<EllOp<double>, double>(h, which, x, y)
-         : d3    ? run_apply<StencilOp<double, 3>, double>(h, which, x, y)
-                 : run_apply<StencilOp<double, 2>, double>(h, which, x, y);
+    return dispatch(h, [&](auto opk, auto tk) {
+        using Op = typename decltype(opk)::type;
+        using T = typename decltype(tk)::type;
+        return run_apply<Op, T>(h, which, x, y);
+    });
 }
 
 gadi_status gadi_predict_params(gadi_solver *h, const double *features, int32_t nfeat, int32_t kind,

@@ -17,8 +17,10 @@ enum : int {
 // ---------------------------------------------------------------------------
 // Precision traits. T is the storage type of the inner vectors and matrix
 // values; Acc the arithmetic type (FP32 for FP16 storage, FP64 otherwise).
-// Arithmetic uses explicitly rounded multiply and add (no FMA contraction),
-// so every rounding step is the one written in the source.
+// Every rounding step is the one written in the source: FP32 uses separately
+// rounded multiply and add (no contraction); FP64 uses one fused
+// multiply-add per term (madd), which halves the FP64 instructions on a GPU
+// with a low FP64 rate.
 // ---------------------------------------------------------------------------
 template <class T> struct Prec;
 
@@ -32,6 +34,8 @@ template <> struct Prec<__half> {
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    // c + a b
+    static __device__ __forceinline__ float madd(float c, float a, float b) { return __fadd_rn(c, __fmul_rn(a, b)); }
 };
 
 template <> struct Prec<double> {
@@ -43,12 +47,9 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double madd(double c, double a, double b) { return __fma_rn(a, b, c); }
 };
 
-__device__ __forceinline__ double d_madd(double acc, double a, double b)
-{
-    return __dadd_rn(acc, __dmul_rn(a, b));
-}
 
 // ---------------------------------------------------------------------------
 // Timers and ordered memory accesses (inline PTX)
@@ -82,8 +83,21 @@ __device__ __forceinline__ void fence_acq_rel_gpu()
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // Control block of one solve (device memory, zeroed before each launch).
 struct Ctl {
+    unsigned long long arrive;   // grid-barrier arrival counter (monotone within a launch)
     int error;                   // first error code raised on the device (0 = none)
     int status;                  // final gadi_status of the solve
     int outer_iters;
@@ -174,28 +188,27 @@ __device__ __forceinline__ void block_reduce_w0(double (&v)[NS], const int (&ops
 }
 
 // ---------------------------------------------------------------------------
-// Grid all-reduce with a data-carrying barrier. Each block publishes its
-// block result as tagged 64-bit words (epoch << 32 | 32-bit payload): thread
-// 0 issues one release fence (which, after the preceding __syncthreads,
-// orders all of the block's earlier writes) and then relaxed stores. Warp 0
-// of every block loads all blocks' words with relaxed loads, several words
-// per lane at once, until every tag carries the current epoch, then issues
-// one acquire fence and combines the payloads in a fixed order (lane l takes
-// blocks l, l+32, ... ascending, then a fixed shuffle tree). Synchronisation
-// and data exchange take one L2 round trip. Two slot buffers alternate by
-// epoch parity, so a block that runs ahead never overwrites words that a
-// slower block has not read yet.
-// Polling is bounded by wait_ns of %globaltimer: on expiry the block records
-// kErrTimeout in ctl->error, and every block leaves at its next exchange (a
-// block that sees ctl->error stops waiting at once). One block needs no
-// global memory at all.
+// Grid all-reduce. Each block writes its block result to its own partial
+// slots, then thread 0 arrives on a monotone 64-bit counter with a release
+// add (which, after the preceding __syncthreads, publishes every write of
+// the block) and spins with acquire loads until all blocks of this epoch
+// have arrived. Warp 0 then reads all blocks' partials in one batch of
+// independent loads and combines them in a fixed order (lane l takes blocks
+// l, l+32, ... ascending, then a fixed shuffle tree), so every block holds
+// bitwise identical results and takes identical branches. Partials
+// alternate between two buffers by epoch parity, so a block that runs ahead
+// never overwrites partials that a slower block has not read yet.
+// The spin is bounded by wait_ns of %globaltimer: on expiry the block
+// records kErrTimeout in ctl->error and every block leaves at its next
+// exchange (a block that sees ctl->error stops waiting at once). One block
+// needs no global memory at all.
 // ---------------------------------------------------------------------------
 struct GridExchange {
     Ctl *ctl;
-    unsigned long long *slots;     // [2][kMaxWords][gridDim]
+    double *part;                  // [2][kMaxSlots][gridDim]
     unsigned epoch;
     unsigned long long wait_ns;
-    unsigned extra;                // added to the expected tag (never reached: timeout test)
+    unsigned extra;                // added to the arrival target (never reached: timeout test)
 
     template <class V, int NS>
     __device__ __forceinline__ bool allreduce(V (&v)[NS], const int (&ops)[NS])
@@ -214,67 +227,20 @@ struct GridExchange {
             __syncthreads();
             return true;
         }
-        constexpr int WPS = sizeof(V) == 8 ? 2 : 1;
-        constexpr int NWORD = NS * WPS;
-        constexpr int CH = NWORD >= 4 ? 2 : 4;          // blocks per lane per polling round
         ++epoch;
         const unsigned G = gridDim.x;
-        unsigned long long *buf = slots + (size_t)(epoch & 1u) * kMaxWords * G;
-        const unsigned long long tag = (unsigned long long)epoch << 32;
+        double *buf = part + (size_t)(epoch & 1u) * kMaxSlots * G;
         if (threadIdx.x < 32) {
             const int lane = threadIdx.x;
-            if (lane == 0) {
-                fence_acq_rel_gpu();
-#pragma unroll
-                for (int s = 0; s < NS; ++s) {
-                    if (WPS == 2) {
-                        double d = (double)v[s];
-                        st_relaxed_u64(buf + (size_t)(2 * s) * G + blockIdx.x, tag | (unsigned)__double2hiint(d));
-                        st_relaxed_u64(buf + (size_t)(2 * s + 1) * G + blockIdx.x, tag | (unsigned)__double2loint(d));
-                    } else {
-                        st_relaxed_u64(buf + (size_t)s * G + blockIdx.x, tag | (unsigned)__float_as_uint((float)v[s]));
-                    }
-                }
-            }
-            const unsigned long long want = (unsigned long long)(epoch + extra) << 32;
-            V acc[NS];
-#pragma unroll
-            for (int s = 0; s < NS; ++s) acc[s] = V(0);
             int ok = 1;
-            const unsigned long long t0 = global_ns();
-            for (unsigned b0 = lane; b0 < G && ok; b0 += 32 * CH) {
+            if (lane == 0) {
+#pragma unroll
+                for (int s = 0; s < NS; ++s) buf[(size_t)s * G + blockIdx.x] = (double)v[s];
+                red_release_add_u64(&ctl->arrive, 1ULL);
+                const unsigned long long target = (unsigned long long)epoch * G + extra;
+                const unsigned long long t0 = global_ns();
                 unsigned spins = 0;
-                for (;;) {
-                    unsigned long long wd[CH][NWORD];
-                    bool ready = true;
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        const unsigned b = b0 + 32u * c;
-#pragma unroll
-                        for (int w = 0; w < NWORD; ++w)
-                            wd[c][w] = b < G ? ld_relaxed_u64(buf + (size_t)w * G + b) : want;
-                    }
-#pragma unroll
-                    for (int c = 0; c < CH; ++c)
-#pragma unroll
-                        for (int w = 0; w < NWORD; ++w)
-                            ready = ready && ((wd[c][w] & 0xffffffff00000000ULL) == want);
-                    if (ready) {
-#pragma unroll
-                        for (int c = 0; c < CH; ++c) {
-                            if (b0 + 32u * c >= G) continue;
-#pragma unroll
-                            for (int s = 0; s < NS; ++s) {
-                                V val;
-                                if (WPS == 2)
-                                    val = (V)__hiloint2double((int)(unsigned)wd[c][2 * s], (int)(unsigned)wd[c][2 * s + 1]);
-                                else
-                                    val = (V)__uint_as_float((unsigned)wd[c][s]);
-                                acc[s] = red_op(acc[s], val, ops[s]);
-                            }
-                        }
-                        break;
-                    }
+                while (ld_acquire_u64(&ctl->arrive) < target) {
                     if ((++spins & 15u) == 0) {
                         if (ld_volatile_i32(&ctl->error) != 0) { ok = 0; break; }
                         if (global_ns() - t0 > wait_ns) {
@@ -285,8 +251,29 @@ struct GridExchange {
                     }
                 }
             }
-            fence_acq_rel_gpu();
-            ok = __all_sync(0xffffffffu, ok);
+            __syncwarp();
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            V acc[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) acc[s] = V(0);
+            if (ok) {
+                constexpr int CH = 4;
+                for (unsigned b0 = lane; b0 < G; b0 += 32 * CH) {
+                    double w[CH][NS];
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) {
+                            const unsigned b = b0 + 32u * c;
+                            w[c][s] = b < G ? __ldcg(buf + (size_t)s * G + b) : 0.0;
+                        }
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+                        if (b0 + 32u * c < G)
+#pragma unroll
+                            for (int s = 0; s < NS; ++s) acc[s] = red_op(acc[s], (V)w[c][s], ops[s]);
+                }
+            }
             warp_tree(acc, ops);
             if (lane == 0) {
 #pragma unroll

@@ -1,20 +1,25 @@
-// gadi_ops.cuh -- the operators of GADI-IR as row functions for the
-// persistent kernel.
+// gadi_ops.cuh -- the operators of GADI-IR for the persistent kernel, and the
+// vector expressions they are applied to.
 //
-//   which = kOpA  : (A x)_i                       FP64 (outer residual, Alg. 1 step 1)
-//   which = kOpH  : (H' x)_i = 2^-sM (aI + M) x   inner precision (Alg. 1 step 2)
-//   which = kOpS  : (S' x)_i = 2^-sN (aI + N) x   inner precision (Alg. 1 step 3)
-//   which = kOpST : (S'^T x)_i                    (CGNR's transpose product)
+//   kOpA  : (A x)_i                       FP64 (outer residual, Alg. 1 step 1)
+//   kOpH  : (H' x)_i = 2^-sM (aI + M) x   inner precision (Alg. 1 step 2)
+//   kOpS  : (S' x)_i = 2^-sN (aI + N) x   inner precision (Alg. 1 step 3)
+//   kOpST : (S'^T x)_i                    (CGNR's transpose product)
+//
+// Work is done in items of R consecutive rows (R = 1 for the general sparse
+// operator, R = 8 for the stencil when the grid side is a multiple of 8:
+// one 16-byte FP16 load per vector and one coordinate computation per item).
 //
 // A row is evaluated as sigma*f(i) first, then the matrix entries in
-// ascending column order (the CSR order), with explicitly rounded products
-// and sums. For FP16 values and vectors each product is exact in FP32, so a
-// row equals the FP32 sum of the same terms in the same order on any device.
+// ascending column order (the CSR order). Inner precision FP16: products of
+// two FP16 values are exact in FP32, sums are explicitly rounded FP32 adds.
+// FP64 (residual, FP64 inner path): each term is one fused multiply-add.
+// So a row equals, bit for bit, the same sum formed on the CPU.
 //
-// f(j) supplies the vector value at column j as an Acc; the persistent
-// kernel passes expressions (e.g. r_j + beta p_j rounded to storage) so that
-// the vector update of a Krylov step can be fused into the next product
-// without an extra grid barrier.
+// The vector argument is an expression object with one(j) (value at column
+// j) and eight(j0, out) (values at j0..j0+7, j0 a multiple of 8); the kernel
+// passes expressions such as "r + beta p rounded to FP16" so that vector
+// updates of a Krylov step fuse into the next operator application.
 #pragma once
 
 #include "gadi_device.cuh"
@@ -22,6 +27,165 @@
 namespace gadi {
 
 enum : int { kOpA = 0, kOpH = 1, kOpS = 2, kOpST = 3 };
+
+// ---------------------------------------------------------------------------
+// 8-wide loads and stores of FP16 / FP64 vectors (16-byte transactions)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ld8(const __half *p, int64_t j0, float (&o)[8])
+{
+    const uint4 u = *reinterpret_cast<const uint4 *>(p + j0);
+    const __half2 *h = reinterpret_cast<const __half2 *>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float2 f = __half22float2(h[k]);
+        o[2 * k] = f.x;
+        o[2 * k + 1] = f.y;
+    }
+}
+
+__device__ __forceinline__ void st8(__half *p, int64_t j0, const float (&v)[8])
+{
+    uint4 u;
+    __half2 *h = reinterpret_cast<__half2 *>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __halves2half2(__float2half_rn(v[2 * k]), __float2half_rn(v[2 * k + 1]));
+    *reinterpret_cast<uint4 *>(p + j0) = u;
+}
+
+__device__ __forceinline__ void ld8(const double *p, int64_t j0, double (&o)[8])
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p + j0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double2 d = q[k];
+        o[2 * k] = d.x;
+        o[2 * k + 1] = d.y;
+    }
+}
+
+__device__ __forceinline__ void st8(double *p, int64_t j0, const double (&v)[8])
+{
+    double2 *q = reinterpret_cast<double2 *>(p + j0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+
+// own-row access of an item of R rows; values rounded to T on store
+template <class T, int R>
+struct ItemIO {
+    using Acc = typename Prec<T>::Acc;
+    static __device__ __forceinline__ void ld(const T *p, int64_t item, Acc (&o)[R])
+    {
+        if constexpr (R == 8) ld8(p, item * 8, o);
+        else o[0] = Prec<T>::ld(p[item]);
+    }
+    static __device__ __forceinline__ void st(T *p, int64_t item, const Acc (&v)[R])
+    {
+        if constexpr (R == 8) st8(p, item * 8, v);
+        else p[item] = Prec<T>::st(v[0]);
+    }
+};
+
+template <int R>
+struct ItemIO64 {
+    static __device__ __forceinline__ void ld(const double *p, int64_t item, double (&o)[R])
+    {
+        if constexpr (R == 8) ld8(p, item * 8, o);
+        else o[0] = p[item];
+    }
+    static __device__ __forceinline__ void st(double *p, int64_t item, const double (&v)[R])
+    {
+        if constexpr (R == 8) st8(p, item * 8, v);
+        else p[item] = v[0];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Vector expressions (value of an inner-precision vector at column j)
+// ---------------------------------------------------------------------------
+template <class T>
+struct XLoad {                       // a
+    using Acc = typename Prec<T>::Acc;
+    const T *a;
+    __device__ __forceinline__ Acc one(int64_t j) const { return Prec<T>::ld(a[j]); }
+    __device__ __forceinline__ void eight(int64_t j0, Acc (&o)[8]) const { ld8(a, j0, o); }
+};
+
+template <class T>
+struct XAxpy {                       // fl(a + c b)
+    using Acc = typename Prec<T>::Acc;
+    using P = Prec<T>;
+    const T *a, *b;
+    Acc c;
+    __device__ __forceinline__ Acc one(int64_t j) const { return P::rnd(P::madd(P::ld(a[j]), c, P::ld(b[j]))); }
+    __device__ __forceinline__ void eight(int64_t j0, Acc (&o)[8]) const
+    {
+        Acc x[8], y[8];
+        ld8(a, j0, x);
+        ld8(b, j0, y);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = P::rnd(P::madd(x[k], c, y[k]));
+    }
+};
+
+template <class T>
+struct XAxpy2 {                      // fl(a - c fl(b + d e))  (C-G residual update, fused)
+    using Acc = typename Prec<T>::Acc;
+    using P = Prec<T>;
+    const T *a, *b, *e;
+    Acc c, d;
+    __device__ __forceinline__ Acc one(int64_t j) const
+    {
+        const Acc s = P::rnd(P::madd(P::ld(b[j]), d, P::ld(e[j])));
+        return P::rnd(P::madd(P::ld(a[j]), -c, s));
+    }
+    __device__ __forceinline__ void eight(int64_t j0, Acc (&o)[8]) const
+    {
+        Acc x[8], y[8], w[8];
+        ld8(a, j0, x);
+        ld8(b, j0, y);
+        ld8(e, j0, w);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = P::rnd(P::madd(x[k], -c, P::rnd(P::madd(y[k], d, w[k]))));
+    }
+};
+
+template <class T>
+struct XScale {                      // fl(c a), c a power of two
+    using Acc = typename Prec<T>::Acc;
+    using P = Prec<T>;
+    const T *a;
+    Acc c;
+    __device__ __forceinline__ Acc one(int64_t j) const { return P::rnd(P::mul(P::ld(a[j]), c)); }
+    __device__ __forceinline__ void eight(int64_t j0, Acc (&o)[8]) const
+    {
+        Acc x[8];
+        ld8(a, j0, x);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = P::rnd(P::mul(x[k], c));
+    }
+};
+
+template <class T>
+struct XDemote {                     // fl_T(2^-e r), r in FP64 (Alg. 1: r^ = fl_r(s^))
+    using Acc = typename Prec<T>::Acc;
+    const double *r;
+    double sc;
+    __device__ __forceinline__ Acc one(int64_t j) const { return Prec<T>::ld(Prec<T>::from64(r[j] * sc)); }
+    __device__ __forceinline__ void eight(int64_t j0, Acc (&o)[8]) const
+    {
+        double x[8];
+        ld8(r, j0, x);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = Prec<T>::ld(Prec<T>::from64(x[k] * sc));
+    }
+};
+
+struct XLoad64 {
+    const double *a;
+    __device__ __forceinline__ double one(int64_t j) const { return a[j]; }
+    __device__ __forceinline__ void eight(int64_t j0, double (&o)[8]) const { ld8(a, j0, o); }
+};
 
 // ---------------------------------------------------------------------------
 // General sparse matrix in row-major ELL form built from the CSR input:
@@ -34,6 +198,7 @@ enum : int { kOpA = 0, kOpH = 1, kOpS = 2, kOpST = 3 };
 template <class T>
 struct EllOp {
     using Acc = typename Prec<T>::Acc;
+    static constexpr int R = 1;
     int64_t n;
     int W;
     const int *__restrict__ col;
@@ -44,17 +209,17 @@ struct EllOp {
     Acc sigH, sigS;                   // 2^-sM alpha, 2^-sN alpha
 
     template <class F>
-    __device__ __forceinline__ double rowA(int64_t i, F f) const
+    __device__ __forceinline__ void rowsA(int64_t i, const F &f, double (&out)[1]) const
     {
         const int *c = col + i * W;
         const double *v = a64 + i * W;
         double acc = 0.0;
-        for (int k = 0; k < W; ++k) acc = d_madd(acc, __ldg(v + k), f(__ldg(c + k)));
-        return acc;
+        for (int k = 0; k < W; ++k) acc = __fma_rn(__ldg(v + k), f.one(__ldg(c + k)), acc);
+        out[0] = acc;
     }
 
     template <class F>
-    __device__ __forceinline__ Acc row(int which, int64_t i, F f) const
+    __device__ __forceinline__ void rows(int which, int64_t i, const F &f, Acc (&out)[1]) const
     {
         using P = Prec<T>;
         const int *c = col + i * W;
@@ -65,38 +230,35 @@ struct EllOp {
         else if (nt) { v = nt; sig = sigS; }
         else { v = nv; sig = sigS; sgn = Acc(-1); }
         v += i * W;
-        Acc acc = P::mul(sig, f(i));
-        for (int k = 0; k < W; ++k) {
-            Acc val = P::ld(v[k]);
-            acc = P::add(acc, P::mul(sgn * val, f(__ldg(c + k))));
-        }
-        return acc;
+        Acc acc = P::mul(sig, f.one(i));
+        for (int k = 0; k < W; ++k) acc = P::madd(acc, sgn * P::ld(v[k]), f.one(__ldg(c + k)));
+        out[0] = acc;
     }
 };
 
 // ---------------------------------------------------------------------------
 // Matrix-free 5-point (2D) / 7-point (3D) convection-diffusion operator of
-// §4.1 on an N^dim grid, x fastest. Constant-k form: all coefficients are
-// scalars. Face form: per-node arrays of the diagonal and of the upper-face
-// couplings per axis, taken from the HSS split values (M symmetric, so the
-// lower coupling of node i along d is the upper coupling of node i - e_d).
-// The convection part N is the constant c = beta h / 2 in both forms.
+// §4.1 on an N^dim grid, x fastest; R = 8 needs N % 8 == 0 (an item is 8
+// nodes of one x-line). Constant-k form: scalar coefficients. Face form:
+// per-node arrays of the diagonal and of the upper-face couplings per axis
+// (M is symmetric, so the lower coupling of node i along d is the upper
+// coupling of node i - e_d). N is the constant convection c in both forms.
 // ---------------------------------------------------------------------------
-template <class T, int DIM>
+template <class T, int DIM, int RR>
 struct StencilOp {
     using Acc = typename Prec<T>::Acc;
     static constexpr int kDim = DIM;
-    int dim, N;          // dim == DIM
+    static constexpr int R = RR;
+    int dim, N;
     int64_t n;
-    // FP64 A for the residual: constant form uses (a_diag, a_lo, a_hi);
-    // face form uses AD[i] and AL[d][i] = a_{i,i-e_d}, AU[d][i] = a_{i,i+e_d}
+    // FP64 A for the residual: constant form (a_diag, a_lo, a_hi); face form
+    // AD[i], AL[d][i] = a_{i,i-e_d}, AU[d][i] = a_{i,i+e_d}
     double a_diag, a_lo, a_hi;
     const double *__restrict__ AD;
     const double *__restrict__ AL[3];
     const double *__restrict__ AU[3];
-    // inner operators: H' diagonal/off-diagonal (constant form) or arrays
-    // HD[i] = 2^-sM m_ii, HK[d][i] = 2^-sM m_{i,i+e_d} (face form);
-    // S': 2^-sN c rounded to T
+    // inner: constant form (h_diag, h_off); face form HD[i] = 2^-sM m_ii,
+    // HK[d][i] = 2^-sM m_{i,i+e_d}; S' coupling 2^-sN c rounded to T
     Acc h_diag, h_off, s_c;
     const T *__restrict__ HD;
     const T *__restrict__ HK[3];
@@ -123,8 +285,9 @@ struct StencilOp {
         return d == 0 ? 1 : (d == 1 ? (int64_t)N : (int64_t)N * N);
     }
 
+    // ---- scalar rows (R == 1) ------------------------------------------------
     template <class F>
-    __device__ __forceinline__ double rowA(int64_t i, F f) const
+    __device__ __forceinline__ double rowA1(int64_t i, const F &f) const
     {
         unsigned cd[3];
         coords(i, cd);
@@ -133,45 +296,198 @@ struct StencilOp {
         const bool face = AD != nullptr;
 #pragma unroll
         for (int d = DIM - 1; d >= 0; --d)
-            if (cd[d] > 0) acc = d_madd(acc, face ? __ldg(AL[d] + i) : a_lo, f(i - stride(d)));
-        acc = d_madd(acc, face ? __ldg(AD + i) : a_diag, f(i));
+            if (cd[d] > 0) acc = __fma_rn(face ? __ldg(AL[d] + i) : a_lo, f.one(i - stride(d)), acc);
+        acc = __fma_rn(face ? __ldg(AD + i) : a_diag, f.one(i), acc);
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
-            if (cd[d] < last) acc = d_madd(acc, face ? __ldg(AU[d] + i) : a_hi, f(i + stride(d)));
+            if (cd[d] < last) acc = __fma_rn(face ? __ldg(AU[d] + i) : a_hi, f.one(i + stride(d)), acc);
         return acc;
     }
 
     template <class F>
-    __device__ __forceinline__ Acc row(int which, int64_t i, F f) const
+    __device__ __forceinline__ Acc row1(int which, int64_t i, const F &f) const
     {
         using P = Prec<T>;
         unsigned cd[3];
         coords(i, cd);
         const unsigned last = (unsigned)N - 1;
-        const Acc fi = f(i);
+        const Acc fi = f.one(i);
         if (which == kOpH) {
             const bool face = HD != nullptr;
             Acc acc = P::mul(sigH, fi);
 #pragma unroll
             for (int d = DIM - 1; d >= 0; --d)
                 if (cd[d] > 0)
-                    acc = P::add(acc, P::mul(face ? P::ld(HK[d][i - stride(d)]) : h_off, f(i - stride(d))));
-            acc = P::add(acc, P::mul(face ? P::ld(HD[i]) : h_diag, fi));
+                    acc = P::madd(acc, face ? P::ld(HK[d][i - stride(d)]) : h_off, f.one(i - stride(d)));
+            acc = P::madd(acc, face ? P::ld(HD[i]) : h_diag, fi);
 #pragma unroll
             for (int d = 0; d < DIM; ++d)
-                if (cd[d] < last) acc = P::add(acc, P::mul(face ? P::ld(HK[d][i]) : h_off, f(i + stride(d))));
+                if (cd[d] < last) acc = P::madd(acc, face ? P::ld(HK[d][i]) : h_off, f.one(i + stride(d)));
             return acc;
         }
-        // S' (lower -c, upper +c) or S'^T (lower +c, upper -c); N has a zero diagonal
         const Acc lo = which == kOpS ? -s_c : s_c;
         Acc acc = P::mul(sigS, fi);
 #pragma unroll
         for (int d = DIM - 1; d >= 0; --d)
-            if (cd[d] > 0) acc = P::add(acc, P::mul(lo, f(i - stride(d))));
+            if (cd[d] > 0) acc = P::madd(acc, lo, f.one(i - stride(d)));
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
-            if (cd[d] < last) acc = P::add(acc, P::mul(-lo, f(i + stride(d))));
+            if (cd[d] < last) acc = P::madd(acc, -lo, f.one(i + stride(d)));
         return acc;
+    }
+
+    // ---- 8-row items (R == 8) -----------------------------------------------
+    // Items of 8: neighbours along y and z are whole aligned chunks; along x
+    // they are the item's own values shifted by one, with the two ends from
+    // one().
+    template <class F>
+    __device__ __forceinline__ void rowsA(int64_t item, const F &f, double (&out)[R]) const
+    {
+        if constexpr (R == 1) {
+            out[0] = rowA1(item, f);
+        } else {
+            const int64_t i0 = item * 8;
+            unsigned cd[3];
+            coords(i0, cd);
+            const unsigned last = (unsigned)N - 1;
+            const bool face = AD != nullptr;
+            double c[8], acc[8], t[8], cf[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+            f.eight(i0, c);
+#pragma unroll
+            for (int d = DIM - 1; d >= 1; --d)
+                if (cd[d] > 0) {
+                    f.eight(i0 - stride(d), t);
+                    if (face) ld8(AL[d], i0, cf);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(face ? cf[k] : a_lo, t[k], acc[k]);
+                }
+            {   // x lower
+                const double xm = cd[0] > 0 ? f.one(i0 - 1) : 0.0;
+                if (face) ld8(AL[0], i0, cf);
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (k > 0 || cd[0] > 0) acc[k] = __fma_rn(face ? cf[k] : a_lo, k ? c[k - 1] : xm, acc[k]);
+            }
+            if (face) ld8(AD, i0, cf);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(face ? cf[k] : a_diag, c[k], acc[k]);
+            {   // x upper
+                const double xp = cd[0] + 8 <= last ? f.one(i0 + 8) : 0.0;
+                if (face) ld8(AU[0], i0, cf);
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (k < 7 || cd[0] + 8 <= last) acc[k] = __fma_rn(face ? cf[k] : a_hi, k < 7 ? c[k + 1] : xp, acc[k]);
+            }
+#pragma unroll
+            for (int d = 1; d < DIM; ++d)
+                if (cd[d] < last) {
+                    f.eight(i0 + stride(d), t);
+                    if (face) ld8(AU[d], i0, cf);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(face ? cf[k] : a_hi, t[k], acc[k]);
+                }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) out[k] = acc[k];
+        }
+    }
+
+    template <class F>
+    __device__ __forceinline__ void rows(int which, int64_t item, const F &f, Acc (&out)[R]) const
+    {
+        using P = Prec<T>;
+        if constexpr (R == 1) {
+            out[0] = row1(which, item, f);
+        } else {
+            const int64_t i0 = item * 8;
+            unsigned cd[3];
+            coords(i0, cd);
+            const unsigned last = (unsigned)N - 1;
+            Acc c[8], acc[8], t[8], cf[8];
+            f.eight(i0, c);
+            if (which == kOpH) {
+                const bool face = HD != nullptr;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] = P::mul(sigH, c[k]);
+#pragma unroll
+                for (int d = DIM - 1; d >= 1; --d)
+                    if (cd[d] > 0) {
+                        f.eight(i0 - stride(d), t);
+                        if (face) ld8(HK[d], i0 - stride(d), cf);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], face ? cf[k] : h_off, t[k]);
+                    }
+                {   // x lower: coupling of node i with i-1 is HK[0][i-1]
+                    const Acc xm = cd[0] > 0 ? f.one(i0 - 1) : Acc(0);
+                    Acc c0 = h_off;
+                    if (face) {
+                        ld8(HK[0], i0, cf);
+                        c0 = cd[0] > 0 ? P::ld(HK[0][i0 - 1]) : Acc(0);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (k > 0 || cd[0] > 0)
+                            acc[k] = P::madd(acc[k], face ? (k ? cf[k - 1] : c0) : h_off, k ? c[k - 1] : xm);
+                }
+                if (face) {
+                    Acc dg[8];
+                    ld8(HD, i0, dg);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], dg[k], c[k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], h_diag, c[k]);
+                }
+                {   // x upper: coupling HK[0][i]
+                    const Acc xp = cd[0] + 8 <= last ? f.one(i0 + 8) : Acc(0);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (k < 7 || cd[0] + 8 <= last)
+                            acc[k] = P::madd(acc[k], face ? cf[k] : h_off, k < 7 ? c[k + 1] : xp);
+                }
+#pragma unroll
+                for (int d = 1; d < DIM; ++d)
+                    if (cd[d] < last) {
+                        f.eight(i0 + stride(d), t);
+                        if (face) ld8(HK[d], i0, cf);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], face ? cf[k] : h_off, t[k]);
+                    }
+            } else {
+                const Acc lo = which == kOpS ? -s_c : s_c;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] = P::mul(sigS, c[k]);
+#pragma unroll
+                for (int d = DIM - 1; d >= 1; --d)
+                    if (cd[d] > 0) {
+                        f.eight(i0 - stride(d), t);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], lo, t[k]);
+                    }
+                {
+                    const Acc xm = cd[0] > 0 ? f.one(i0 - 1) : Acc(0);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (k > 0 || cd[0] > 0) acc[k] = P::madd(acc[k], lo, k ? c[k - 1] : xm);
+                }
+                {
+                    const Acc xp = cd[0] + 8 <= last ? f.one(i0 + 8) : Acc(0);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (k < 7 || cd[0] + 8 <= last) acc[k] = P::madd(acc[k], -lo, k < 7 ? c[k + 1] : xp);
+                }
+#pragma unroll
+                for (int d = 1; d < DIM; ++d)
+                    if (cd[d] < last) {
+                        f.eight(i0 + stride(d), t);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], -lo, t[k]);
+                    }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) out[k] = acc[k];
+        }
     }
 };
 

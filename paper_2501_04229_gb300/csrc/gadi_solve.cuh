@@ -2,23 +2,26 @@
 //
 // One cooperative launch runs the whole solve: the outer refinement loop
 // and both inner Krylov solves. Phases over the rows are separated by the
-// bounded grid barrier of gadi_device.cuh; every reduction is combined by
-// all blocks identically, so all blocks take the same branches and the
-// scalars of CG and CGNR never leave the device.
+// grid all-reduce of gadi_device.cuh (bounded waits); all blocks hold
+// identical scalars, so they take identical branches and the Krylov scalars
+// never leave the device.
 //
-// Outer step k (Algorithm 1, with the readings of the library header):
-//   R  r = b - A x in FP64, ||r||_inf, ||r||_2^2, ||x||_inf; stopping test
-//   D  e = floor(log2 ||r||_inf); r^ = fl_r(2^-e r)       (§2.2: r^ = fl_r(s^))
-//   CG on H' = 2^-sM (aI + M):  z ~ H'^-1 r^              (Alg. 1 step 2)
-//   C0 ez = floor(log2 ||z||_inf); z^ = 2^-ez z; s = S'^T z^
-//   CGNR on S' = 2^-sN (aI + N): y ~ S'^-1 z^             (Alg. 1 step 3)
-//   U  x += (2-w) a 2^(e - sM + ez - sN) y  in FP64       (Alg. 1 step 4)
+// Outer step k:
+//   R   r = b - A x in FP64; ||r||_inf, ||r||_2^2, ||x||_inf; stopping test
+//   D   e = floor(log2 ||r||_inf), r^ = fl_r(2^-e r) (§2.2: r^ = fl_r(s^));
+//       CG start u = H' r^
+//   CG  on H' = 2^-sM (aI + M): z ~ H'^-1 r^              (Alg. 1 step 2)
+//   C0  ez = floor(log2 ||z||_inf), z^ = 2^-ez z, s = S'^T z^
+//   CGNR on S' = 2^-sN (aI + N): y ~ S'^-1 z^            (Alg. 1 step 3)
+//   U   x += (2-w) a 2^(e - sM + ez - sN) y in FP64       (Alg. 1 step 4)
 // With FP64 inner precision the scales are all 2^0.
 //
-// Barrier count per CG iteration: 2 (the search-direction update
-// p = r + beta p is recomputed at the neighbours inside the next operator
-// application instead of in a phase of its own); per CGNR iteration: 2
-// (likewise, and the residual update is fused with the S^T product).
+// CG is the single-reduction (Chronopoulos-Gear) form: one exchange per
+// iteration; the residual update is recomputed at the neighbours inside the
+// operator application, so r_{i+1} and u_{i+1} = H' r_{i+1} come out of one
+// pass. CGNR (CG on S'^T S') needs two exchanges per iteration; its
+// search-direction and residual updates are fused into the products the
+// same way.
 #pragma once
 
 #include "gadi_ops.cuh"
@@ -28,60 +31,88 @@ namespace gadi {
 template <class Op, class T>
 struct SolveArgs {
     Op op;
-    int64_t n;
+    int64_t n, nitems;
     const double *b;
     double *x;
     double *r64;
-    T *rc, *pA, *pB, *q, *z, *rsA, *rsB, *s, *y;
+    T *v[9];                     // inner work vectors, n elements each
     double anorm, bnorm, tol, eps, pfac;
     int sM, sN, half, stop_kind;
     int max_inner, max_outer;
     Ctl *ctl;
-    unsigned long long *slots;   // [2][kMaxWords][gridDim] exchange words, zeroed before launch
+    double *part;                // [2][kMaxSlots][gridDim] partial sums
     double *eta_hist;            // optional, max_outer + 1 entries
     unsigned long long wait_ns;
     unsigned extra;
 };
 
+// launch bound: 1024 threads for one-row items, 512 for 8-row items (whose
+// per-thread state is larger)
+template <class Op>
+constexpr int max_threads() { return Op::R == 8 ? 512 : 1024; }
+
 template <class Op, class T>
-__global__ void __launch_bounds__(1024, 1) gadi_solve_kernel(const SolveArgs<Op, T> a)
+__global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const SolveArgs<Op, T> a)
 {
     using P = Prec<T>;
     using Acc = typename P::Acc;
-    const int64_t n = a.n;
+    constexpr int R = Op::R;
+    using IO = ItemIO<T, R>;
+    using IO64 = ItemIO64<R>;
+    const int64_t items = a.nitems;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nt = (int64_t)gridDim.x * blockDim.x;
     const Op &op = a.op;
-    GridExchange ex{a.ctl, a.slots, 0u, a.wait_ns, a.extra};
+    GridExchange ex{a.ctl, a.part, 0u, a.wait_ns, a.extra};
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const Acc eps2 = (Acc)(a.eps * a.eps);
+    const int ops1[1] = {kSum};
+    const int ops2[2] = {kSum, kSum};
+    const int ops3[3] = {kSum, kSum, kMax};
+
+    // work vectors: CG uses r (2), u (2), s (2), p, z; CGNR reuses them
+    T *const z = a.v[8];
 
     double r0 = 0.0, best = INFINITY, eta = 0.0, res = 0.0;
     long long itH = 0, itS = 0, spmv = 0;
     int k = 0, status = kErrNotConverged;
 
     for (;;) {
-        // ---- R: outer residual in FP64 -------------------------------------
+        // ---- R: outer residual in FP64 -----------------------------------------
+        double vR[3] = {0.0, 0.0, 0.0};
         {
-            double v[3] = {0.0, 0.0, 0.0};
-            const int ops[3] = {kMax, kSum, kMax};
-            const double *x = a.x;
-            for (int64_t i = t0; i < n; i += nt) {
-                double ax = op.rowA(i, [&](int64_t j) { return x[j]; });
-                double r = __dsub_rn(a.b[i], ax);
-                a.r64[i] = r;
-                v[0] = fmax(v[0], fabs(r));
-                v[1] = d_madd(v[1], r, r);
-                v[2] = fmax(v[2], fabs(x[i]));
+            double lmax = 0.0, lsum = 0.0, xmax = 0.0;
+            const XLoad64 fx{a.x};
+            for (int64_t it = t0; it < items; it += nt) {
+                double ax[R], bb[R], xx[R], rr[R];
+                op.rowsA(it, fx, ax);
+                IO64::ld(a.b, it, bb);
+                IO64::ld(a.x, it, xx);
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    rr[q] = __dsub_rn(bb[q], ax[q]);
+                    lmax = fmax(lmax, fabs(rr[q]));
+                    lsum = __fma_rn(rr[q], rr[q], lsum);
+                    xmax = fmax(xmax, fabs(xx[q]));
+                }
+                IO64::st(a.r64, it, rr);
             }
-            if (!ex.allreduce(v, ops)) return;
-            ++spmv;
-            const double rinf = v[0], rn2 = sqrt(v[1]), xinf = v[2];
-            const double den = a.anorm * xinf + a.bnorm;
-            eta = den > 0.0 ? rinf / den : (rinf == 0.0 ? 0.0 : INFINITY);
-            if (k == 0) r0 = rn2;
-            res = r0 > 0.0 ? rn2 / r0 : 0.0;
-            if (lead && a.eta_hist) a.eta_hist[k] = eta;
+            vR[0] = lsum;
+            vR[1] = lmax;
+            vR[2] = xmax;
+        }
+        {
+            const int opsR[3] = {kSum, kMax, kMax};
+            if (!ex.allreduce(vR, opsR)) return;
+        }
+        ++spmv;
+        const double rinf = vR[1], rn2 = sqrt(vR[0]), xinf = vR[2];
+        const double den = a.anorm * xinf + a.bnorm;
+        eta = den > 0.0 ? rinf / den : (rinf == 0.0 ? 0.0 : INFINITY);
+        if (k == 0) r0 = rn2;
+        res = r0 > 0.0 ? rn2 / r0 : 0.0;
+        if (lead && a.eta_hist) a.eta_hist[k] = eta;
+        {
             bool done = true;
             if (!isfinite(rn2) || !isfinite(eta)) status = kErrDiverged;
             else {
@@ -93,206 +124,248 @@ __global__ void __launch_bounds__(1024, 1) gadi_solve_kernel(const SolveArgs<Op,
                 else done = false;
             }
             if (done) break;
-
-            // ---- D: scale and round the residual; CG start -----------------
-            const int e = (a.half && rinf > 0.0) ? ilogb(rinf) : 0;
-            const double sc = ldexp(1.0, -e);
-            Acc w[1] = {0};
-            const int ops1[1] = {kSum};
-            {
-                Acc acc = 0;
-                for (int64_t i = t0; i < n; i += nt) {
-                    T vr = P::from64(__dmul_rn(a.r64[i], sc));
-                    a.rc[i] = vr;
-                    a.pA[i] = vr;
-                    a.z[i] = P::st(Acc(0));
-                    Acc f = P::ld(vr);
-                    acc = P::add(acc, P::mul(f, f));
-                }
-                w[0] = acc;
-            }
-            if (!ex.allreduce(w, ops1)) return;
-            const Acc rr0 = (Acc)w[0];
-
-            // ---- CG on H' ----------------------------------------------------
-            Acc zinf = 0;
-            int it = 0;
-            if (rr0 > Acc(0)) {
-                T *pc = a.pA, *pn = a.pB;
-                Acc rho = rr0, beta = 0;
-                bool first = true;
-                for (;;) {
-                    // A: p <- r + beta p (fused), q = H' p, <p, q>
-                    Acc u[1] = {0};
-                    {
-                        Acc acc = 0;
-                        if (first) {
-                            auto fp = [&](int64_t j) -> Acc { return P::ld(pc[j]); };
-                            for (int64_t i = t0; i < n; i += nt) {
-                                T qs = P::st(op.row(kOpH, i, fp));
-                                a.q[i] = qs;
-                                acc = P::add(acc, P::mul(fp(i), P::ld(qs)));
-                            }
-                        } else {
-                            const T *rc = a.rc;
-                            auto fp = [&](int64_t j) -> Acc {
-                                return P::rnd(P::add(P::ld(rc[j]), P::mul(beta, P::ld(pc[j]))));
-                            };
-                            for (int64_t i = t0; i < n; i += nt) {
-                                Acc pi = fp(i);
-                                pn[i] = P::st(pi);
-                                T qs = P::st(op.row(kOpH, i, fp));
-                                a.q[i] = qs;
-                                acc = P::add(acc, P::mul(pi, P::ld(qs)));
-                            }
-                        }
-                        u[0] = acc;
-                    }
-                    if (!ex.allreduce(u, ops1)) return;
-                    if (!first) { T *t = pc; pc = pn; pn = t; }
-                    ++it;
-                    ++spmv;
-                    const Acc pq = u[0];
-                    if (!(pq > Acc(0)) || !isfinite((double)pq)) { status = kErrDiverged; break; }
-                    const Acc al = rho / pq;
-                    // B: z += al p, r -= al q, <r, r>, ||z||_inf
-                    Acc vb[2] = {0, 0};
-                    const int opsb[2] = {kSum, kMax};
-                    {
-                        Acc acc = 0, zm = 0;
-                        for (int64_t i = t0; i < n; i += nt) {
-                            Acc zn = P::rnd(P::add(P::ld(a.z[i]), P::mul(al, P::ld(pc[i]))));
-                            a.z[i] = P::st(zn);
-                            Acc rn = P::rnd(P::sub(P::ld(a.rc[i]), P::mul(al, P::ld(a.q[i]))));
-                            a.rc[i] = P::st(rn);
-                            acc = P::add(acc, P::mul(rn, rn));
-                            zm = fmax(zm, fabs(zn));
-                        }
-                        vb[0] = acc;
-                        vb[1] = zm;
-                    }
-                    if (!ex.allreduce(vb, opsb)) return;
-                    const Acc rrn = vb[0];
-                    zinf = vb[1];
-                    if (!isfinite((double)rrn)) { status = kErrDiverged; break; }
-                    if (rrn <= eps2 * rr0 || it >= a.max_inner) break;
-                    beta = rrn / rho;
-                    rho = rrn;
-                    first = false;
-                }
-                if (status == kErrDiverged) break;
-            }
-            itH += it;
-
-            // ---- C0: rescale z, CGNR start (s = S'^T z^, p = s, y = 0) --------
-            const int ez = (a.half && zinf > Acc(0) && isfinite((double)zinf)) ? ilogb((double)zinf) : 0;
-            const Acc scz = (Acc)ldexp(1.0, -ez);
-            Acc c0[2] = {0, 0};
-            const int opsc[2] = {kSum, kSum};
-            {
-                const T *z = a.z;
-                auto fz = [&](int64_t j) -> Acc { return P::rnd(P::mul(P::ld(z[j]), scz)); };
-                Acc acc0 = 0, acc1 = 0;
-                for (int64_t i = t0; i < n; i += nt) {
-                    Acc rs = fz(i);
-                    a.rsA[i] = P::st(rs);
-                    Acc si = P::rnd(op.row(kOpST, i, fz));
-                    a.s[i] = P::st(si);
-                    a.pA[i] = P::st(si);
-                    a.y[i] = P::st(Acc(0));
-                    acc0 = P::add(acc0, P::mul(rs, rs));
-                    acc1 = P::add(acc1, P::mul(si, si));
-                }
-                c0[0] = acc0;
-                c0[1] = acc1;
-            }
-            if (!ex.allreduce(c0, opsc)) return;
-            const Acc rr0s = c0[0];
-
-            // ---- CGNR on S' ------------------------------------------------------
-            it = 0;
-            if (rr0s > Acc(0)) {
-                ++spmv;
-                T *pc = a.pA, *pn = a.pB, *rsc = a.rsA, *rsn = a.rsB;
-                Acc gam = c0[1], beta = 0;
-                bool first = true;
-                for (;;) {
-                    // A: p <- s + beta p (fused), q = S' p, <q, q>
-                    Acc u[1] = {0};
-                    {
-                        Acc acc = 0;
-                        if (first) {
-                            auto fp = [&](int64_t j) -> Acc { return P::ld(pc[j]); };
-                            for (int64_t i = t0; i < n; i += nt) {
-                                Acc qi = P::rnd(op.row(kOpS, i, fp));
-                                a.q[i] = P::st(qi);
-                                acc = P::add(acc, P::mul(qi, qi));
-                            }
-                        } else {
-                            const T *s = a.s;
-                            auto fp = [&](int64_t j) -> Acc {
-                                return P::rnd(P::add(P::ld(s[j]), P::mul(beta, P::ld(pc[j]))));
-                            };
-                            for (int64_t i = t0; i < n; i += nt) {
-                                pn[i] = P::st(fp(i));
-                                Acc qi = P::rnd(op.row(kOpS, i, fp));
-                                a.q[i] = P::st(qi);
-                                acc = P::add(acc, P::mul(qi, qi));
-                            }
-                        }
-                        u[0] = acc;
-                    }
-                    if (!ex.allreduce(u, ops1)) return;
-                    if (!first) { T *t = pc; pc = pn; pn = t; }
-                    ++it;
-                    ++spmv;
-                    const Acc qq = u[0];
-                    if (!(qq > Acc(0)) || !isfinite((double)qq)) { status = kErrDiverged; break; }
-                    const Acc ac = gam / qq;
-                    // B: y += ac p; rs' = rs - ac q (fused into s = S'^T rs')
-                    Acc vb[2] = {0, 0};
-                    {
-                        const T *q = a.q;
-                        const T *rcur = rsc;
-                        auto frs = [&](int64_t j) -> Acc {
-                            return P::rnd(P::sub(P::ld(rcur[j]), P::mul(ac, P::ld(q[j]))));
-                        };
-                        Acc acc0 = 0, acc1 = 0;
-                        for (int64_t i = t0; i < n; i += nt) {
-                            Acc yn = P::rnd(P::add(P::ld(a.y[i]), P::mul(ac, P::ld(pc[i]))));
-                            a.y[i] = P::st(yn);
-                            Acc rn = frs(i);
-                            rsn[i] = P::st(rn);
-                            Acc si = P::rnd(op.row(kOpST, i, frs));
-                            a.s[i] = P::st(si);
-                            acc0 = P::add(acc0, P::mul(rn, rn));
-                            acc1 = P::add(acc1, P::mul(si, si));
-                        }
-                        vb[0] = acc0;
-                        vb[1] = acc1;
-                    }
-                    if (!ex.allreduce(vb, opsc)) return;
-                    { T *t = rsc; rsc = rsn; rsn = t; }
-                    ++spmv;
-                    const Acc rr = vb[0];
-                    if (!isfinite((double)rr)) { status = kErrDiverged; break; }
-                    if (rr <= eps2 * rr0s || it >= a.max_inner) break;
-                    const Acc gn = vb[1];
-                    beta = gn / gam;
-                    gam = gn;
-                    first = false;
-                }
-                if (status == kErrDiverged) break;
-            }
-            itS += it;
-
-            // ---- U: x += (2-w) a 2^(e - sM + ez - sN) y (FP64) ---------------------
-            const double upd = ldexp(a.pfac, e - a.sM + ez - a.sN);
-            for (int64_t i = t0; i < n; i += nt)
-                a.x[i] = __dadd_rn(a.x[i], __dmul_rn(upd, (double)P::ld(a.y[i])));
-            if (!ex.sync()) return;
-            ++k;
         }
+
+        // ---- D: r^ = fl_r(2^-e r), u = H' r^, z = 0 (CG start) ----------------
+        const int e = (a.half && rinf > 0.0) ? ilogb(rinf) : 0;
+        T *rc = a.v[0], *rn = a.v[1], *uc = a.v[2], *un = a.v[3];
+        T *sc = a.v[4], *sn = a.v[5], *p = a.v[6];
+        Acc g[2] = {0, 0};
+        {
+            const XDemote<T> fr{a.r64, ldexp(1.0, -e)};
+            Acc l0 = 0, l1 = 0;
+            for (int64_t it = t0; it < items; it += nt) {
+                Acc rr[R], uu[R], zz[R];
+                op.rows(kOpH, it, fr, uu);
+                if constexpr (R == 8) fr.eight(it * 8, rr);
+                else rr[0] = fr.one(it);
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    uu[q] = P::rnd(uu[q]);
+                    zz[q] = Acc(0);
+                    l0 = P::madd(l0, rr[q], rr[q]);
+                    l1 = P::madd(l1, uu[q], rr[q]);
+                }
+                IO::st(rc, it, rr);
+                IO::st(uc, it, uu);
+                IO::st(z, it, zz);
+            }
+            g[0] = l0;
+            g[1] = l1;
+        }
+        if (!ex.allreduce(g, ops2)) return;
+        ++spmv;
+        const Acc gam0 = g[0];
+
+        // ---- CG on H' (single reduction per iteration) -----------------------------
+        Acc zinf = 0;
+        int it_cg = 0;
+        if (gam0 > Acc(0)) {
+            Acc gam = gam0, del = g[1];
+            if (!(del > Acc(0)) || !isfinite((double)del)) { status = kErrDiverged; break; }
+            Acc al = gam / del, be = 0;
+            bool first = true;
+            for (;;) {
+                // p = r + be p; s = u + be s; z += al p; r' = r - al s; u' = H' r'
+                // (on the first iteration p = r, s = u, and the previous s is not read)
+                Acc w3[3] = {0, 0, 0};
+                auto cg_pass = [&](const auto &frn) {
+                    Acc l0 = 0, l1 = 0, zm = 0;
+                    for (int64_t it = t0; it < items; it += nt) {
+                        Acc r_[R], u_[R], p_[R], s_[R], z_[R], rnew[R], unew[R];
+                        IO::ld(rc, it, r_);
+                        IO::ld(uc, it, u_);
+                        IO::ld(z, it, z_);
+                        if (first) {
+#pragma unroll
+                            for (int q = 0; q < R; ++q) { p_[q] = r_[q]; s_[q] = u_[q]; }
+                        } else {
+                            IO::ld(p, it, p_);
+                            IO::ld(sc, it, s_);
+#pragma unroll
+                            for (int q = 0; q < R; ++q) {
+                                p_[q] = P::rnd(P::madd(r_[q], be, p_[q]));
+                                s_[q] = P::rnd(P::madd(u_[q], be, s_[q]));
+                            }
+                        }
+                        op.rows(kOpH, it, frn, unew);
+#pragma unroll
+                        for (int q = 0; q < R; ++q) {
+                            z_[q] = P::rnd(P::madd(z_[q], al, p_[q]));
+                            rnew[q] = P::rnd(P::madd(r_[q], -al, s_[q]));
+                            unew[q] = P::rnd(unew[q]);
+                            l0 = P::madd(l0, rnew[q], rnew[q]);
+                            l1 = P::madd(l1, unew[q], rnew[q]);
+                            zm = fmax(zm, fabs(z_[q]));
+                        }
+                        IO::st(p, it, p_);
+                        IO::st(sn, it, s_);
+                        IO::st(z, it, z_);
+                        IO::st(rn, it, rnew);
+                        IO::st(un, it, unew);
+                    }
+                    w3[0] = l0;
+                    w3[1] = l1;
+                    w3[2] = zm;
+                };
+                if (first) cg_pass(XAxpy<T>{rc, uc, -al});
+                else cg_pass(XAxpy2<T>{rc, uc, sc, al, be});
+                if (!ex.allreduce(w3, ops3)) return;
+                ++it_cg;
+                ++spmv;
+                { T *t = rc; rc = rn; rn = t; }
+                { T *t = uc; uc = un; un = t; }
+                { T *t = sc; sc = sn; sn = t; }
+                const Acc gn = w3[0], dn = w3[1];
+                zinf = w3[2];
+                if (!isfinite((double)gn) || !isfinite((double)dn)) { status = kErrDiverged; break; }
+                if (gn <= eps2 * gam0 || it_cg >= a.max_inner) break;
+                const Acc bn = gn / gam;
+                const Acc den2 = dn - bn * gn / al;
+                if (!(den2 > Acc(0))) { status = kErrDiverged; break; }
+                al = gn / den2;
+                be = bn;
+                gam = gn;
+                first = false;
+            }
+            if (status == kErrDiverged) break;
+        }
+        itH += it_cg;
+
+        // ---- C0: ez, z^ = 2^-ez z, s = S'^T z^, p = s, y = 0 (CGNR start) -------
+        const int ez = (a.half && zinf > Acc(0) && isfinite((double)zinf)) ? ilogb((double)zinf) : 0;
+        T *rsc = a.v[0], *rsn = a.v[1], *s = a.v[2], *pc = a.v[3], *pn = a.v[4], *q = a.v[5], *y = a.v[6];
+        Acc c0[2] = {0, 0};
+        {
+            const XScale<T> fz{z, (Acc)ldexp(1.0, -ez)};
+            Acc l0 = 0, l1 = 0;
+            for (int64_t it = t0; it < items; it += nt) {
+                Acc rs[R], ss[R], yy[R];
+                if constexpr (R == 8) fz.eight(it * 8, rs);
+                else rs[0] = fz.one(it);
+                op.rows(kOpST, it, fz, ss);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    ss[j] = P::rnd(ss[j]);
+                    yy[j] = Acc(0);
+                    l0 = P::madd(l0, rs[j], rs[j]);
+                    l1 = P::madd(l1, ss[j], ss[j]);
+                }
+                IO::st(rsc, it, rs);
+                IO::st(s, it, ss);
+                IO::st(pc, it, ss);
+                IO::st(y, it, yy);
+            }
+            c0[0] = l0;
+            c0[1] = l1;
+        }
+        if (!ex.allreduce(c0, ops2)) return;
+        const Acc rr0s = c0[0];
+
+        // ---- CGNR on S' ----------------------------------------------------------
+        int it_s = 0;
+        if (rr0s > Acc(0)) {
+            ++spmv;
+            Acc gam = c0[1], be = 0;
+            bool first = true;
+            for (;;) {
+                // A: p = s + be p (fused), q = S' p, <q, q>
+                Acc u1[1] = {0};
+                {
+                    Acc l0 = 0;
+                    if (first) {
+                        const XLoad<T> fp{pc};
+                        for (int64_t it = t0; it < items; it += nt) {
+                            Acc qq[R];
+                            op.rows(kOpS, it, fp, qq);
+#pragma unroll
+                            for (int j = 0; j < R; ++j) {
+                                qq[j] = P::rnd(qq[j]);
+                                l0 = P::madd(l0, qq[j], qq[j]);
+                            }
+                            IO::st(q, it, qq);
+                        }
+                    } else {
+                        const XAxpy<T> fp{s, pc, be};
+                        for (int64_t it = t0; it < items; it += nt) {
+                            Acc pp[R], qq[R];
+                            if constexpr (R == 8) fp.eight(it * 8, pp);
+                            else pp[0] = fp.one(it);
+                            IO::st(pn, it, pp);
+                            op.rows(kOpS, it, fp, qq);
+#pragma unroll
+                            for (int j = 0; j < R; ++j) {
+                                qq[j] = P::rnd(qq[j]);
+                                l0 = P::madd(l0, qq[j], qq[j]);
+                            }
+                            IO::st(q, it, qq);
+                        }
+                    }
+                    u1[0] = l0;
+                }
+                if (!ex.allreduce(u1, ops1)) return;
+                if (!first) { T *t = pc; pc = pn; pn = t; }
+                ++it_s;
+                ++spmv;
+                const Acc qq = u1[0];
+                if (!(qq > Acc(0)) || !isfinite((double)qq)) { status = kErrDiverged; break; }
+                const Acc ac = gam / qq;
+                // B: y += ac p; rs' = rs - ac q; s = S'^T rs' (rs' recomputed at the neighbours)
+                Acc vb[2] = {0, 0};
+                {
+                    const XAxpy<T> frs{rsc, q, -ac};
+                    Acc l0 = 0, l1 = 0;
+                    for (int64_t it = t0; it < items; it += nt) {
+                        Acc yy[R], pp[R], rn_[R], ss[R];
+                        IO::ld(y, it, yy);
+                        IO::ld(pc, it, pp);
+                        if constexpr (R == 8) frs.eight(it * 8, rn_);
+                        else rn_[0] = frs.one(it);
+                        op.rows(kOpST, it, frs, ss);
+#pragma unroll
+                        for (int j = 0; j < R; ++j) {
+                            yy[j] = P::rnd(P::madd(yy[j], ac, pp[j]));
+                            ss[j] = P::rnd(ss[j]);
+                            l0 = P::madd(l0, rn_[j], rn_[j]);
+                            l1 = P::madd(l1, ss[j], ss[j]);
+                        }
+                        IO::st(y, it, yy);
+                        IO::st(rsn, it, rn_);
+                        IO::st(s, it, ss);
+                    }
+                    vb[0] = l0;
+                    vb[1] = l1;
+                }
+                if (!ex.allreduce(vb, ops2)) return;
+                { T *t = rsc; rsc = rsn; rsn = t; }
+                ++spmv;
+                const Acc rr = vb[0];
+                if (!isfinite((double)rr)) { status = kErrDiverged; break; }
+                if (rr <= eps2 * rr0s || it_s >= a.max_inner) break;
+                const Acc gn = vb[1];
+                be = gn / gam;
+                gam = gn;
+                first = false;
+            }
+            if (status == kErrDiverged) break;
+        }
+        itS += it_s;
+
+        // ---- U: x += (2-w) a 2^(e - sM + ez - sN) y (FP64) ------------------------
+        {
+            const double upd = ldexp(a.pfac, e - a.sM + ez - a.sN);
+            for (int64_t it = t0; it < items; it += nt) {
+                double xx[R];
+                Acc yy[R];
+                IO64::ld(a.x, it, xx);
+                IO::ld(y, it, yy);
+#pragma unroll
+                for (int j = 0; j < R; ++j) xx[j] = __fma_rn(upd, (double)yy[j], xx[j]);
+                IO64::st(a.x, it, xx);
+            }
+        }
+        if (!ex.sync()) return;
+        ++k;
     }
     if (lead) {
         Ctl *c = a.ctl;
@@ -309,22 +382,28 @@ __global__ void __launch_bounds__(1024, 1) gadi_solve_kernel(const SolveArgs<Op,
 
 // One operator application y = K x (kernel-level tests, bandwidth runs).
 template <class Op, class T>
-__global__ void gadi_apply_kernel(const Op op, int which, const void *xv, void *yv)
+__global__ void gadi_apply_kernel(const Op op, int64_t nitems, int which, const void *xv, void *yv)
 {
     using P = Prec<T>;
-    const int64_t n = op.n;
+    using Acc = typename P::Acc;
+    constexpr int R = Op::R;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nt = (int64_t)gridDim.x * blockDim.x;
     if (which == kOpA) {
-        const double *x = (const double *)xv;
-        double *y = (double *)yv;
-        for (int64_t i = t0; i < n; i += nt) y[i] = op.rowA(i, [&](int64_t j) { return x[j]; });
+        const XLoad64 f{(const double *)xv};
+        for (int64_t it = t0; it < nitems; it += nt) {
+            double o[R];
+            op.rowsA(it, f, o);
+            ItemIO64<R>::st((double *)yv, it, o);
+        }
         return;
     }
-    const T *x = (const T *)xv;
-    T *y = (T *)yv;
-    auto f = [&](int64_t j) { return P::ld(x[j]); };
-    for (int64_t i = t0; i < n; i += nt) y[i] = P::st(op.row(which, i, f));
+    const XLoad<T> f{(const T *)xv};
+    for (int64_t it = t0; it < nitems; it += nt) {
+        Acc o[R];
+        op.rows(which, it, f, o);
+        ItemIO<T, R>::st((T *)yv, it, o);
+    }
 }
 
 }  // namespace gadi
