@@ -36,6 +36,22 @@ template <> struct Prec<__half> {
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     // c + a b
     static __device__ __forceinline__ float madd(float c, float a, float b) { return __fadd_rn(c, __fmul_rn(a, b)); }
+    // round an even number of values through FP16, two per conversion
+    template <int K>
+    static __device__ __forceinline__ void rndv(float (&v)[K])
+    {
+        if constexpr (K % 2 == 0) {
+#pragma unroll
+            for (int k = 0; k < K; k += 2) {
+                const float2 f = __half22float2(__float22half2_rn(make_float2(v[k], v[k + 1])));
+                v[k] = f.x;
+                v[k + 1] = f.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = rnd(v[k]);
+        }
+    }
 };
 
 template <> struct Prec<double> {
@@ -48,6 +64,8 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
     static __device__ __forceinline__ double madd(double c, double a, double b) { return __fma_rn(a, b, c); }
+    template <int K>
+    static __device__ __forceinline__ void rndv(double (&)[K]) {}
 };
 
 

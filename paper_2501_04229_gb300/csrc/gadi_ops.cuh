@@ -48,7 +48,7 @@ __device__ __forceinline__ void st8(__half *p, int64_t j0, const float (&v)[8])
     uint4 u;
     __half2 *h = reinterpret_cast<__half2 *>(&u);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) h[k] = __halves2half2(__float2half_rn(v[2 * k]), __float2half_rn(v[2 * k + 1]));
+    for (int k = 0; k < 4; ++k) h[k] = __float22half2_rn(make_float2(v[2 * k], v[2 * k + 1]));
     *reinterpret_cast<uint4 *>(p + j0) = u;
 }
 
@@ -124,7 +124,8 @@ struct XAxpy {                       // fl(a + c b)
         ld8(a, j0, x);
         ld8(b, j0, y);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = P::rnd(P::madd(x[k], c, y[k]));
+        for (int k = 0; k < 8; ++k) o[k] = P::madd(x[k], c, y[k]);
+        P::rndv(o);
     }
 };
 
@@ -146,7 +147,11 @@ struct XAxpy2 {                      // fl(a - c fl(b + d e))  (C-G residual upd
         ld8(b, j0, y);
         ld8(e, j0, w);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = P::rnd(P::madd(x[k], -c, P::rnd(P::madd(y[k], d, w[k]))));
+        for (int k = 0; k < 8; ++k) w[k] = P::madd(y[k], d, w[k]);
+        P::rndv(w);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = P::madd(x[k], -c, w[k]);
+        P::rndv(o);
     }
 };
 
@@ -162,7 +167,8 @@ struct XScale {                      // fl(c a), c a power of two
         Acc x[8];
         ld8(a, j0, x);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = P::rnd(P::mul(x[k], c));
+        for (int k = 0; k < 8; ++k) o[k] = P::mul(x[k], c);
+        P::rndv(o);
     }
 };
 

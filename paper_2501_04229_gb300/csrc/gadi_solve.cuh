@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const 
                 op.rows(kOpH, it, fr, uu);
                 if constexpr (R == 8) fr.eight(it * 8, rr);
                 else rr[0] = fr.one(it);
+                P::rndv(uu);
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
-                    uu[q] = P::rnd(uu[q]);
                     zz[q] = Acc(0);
                     l0 = P::madd(l0, rr[q], rr[q]);
                     l1 = P::madd(l1, uu[q], rr[q]);
@@ -184,16 +184,23 @@ __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const 
                             IO::ld(sc, it, s_);
 #pragma unroll
                             for (int q = 0; q < R; ++q) {
-                                p_[q] = P::rnd(P::madd(r_[q], be, p_[q]));
-                                s_[q] = P::rnd(P::madd(u_[q], be, s_[q]));
+                                p_[q] = P::madd(r_[q], be, p_[q]);
+                                s_[q] = P::madd(u_[q], be, s_[q]);
                             }
+                            P::rndv(p_);
+                            P::rndv(s_);
                         }
                         op.rows(kOpH, it, frn, unew);
 #pragma unroll
                         for (int q = 0; q < R; ++q) {
-                            z_[q] = P::rnd(P::madd(z_[q], al, p_[q]));
-                            rnew[q] = P::rnd(P::madd(r_[q], -al, s_[q]));
-                            unew[q] = P::rnd(unew[q]);
+                            z_[q] = P::madd(z_[q], al, p_[q]);
+                            rnew[q] = P::madd(r_[q], -al, s_[q]);
+                        }
+                        P::rndv(z_);
+                        P::rndv(rnew);
+                        P::rndv(unew);
+#pragma unroll
+                        for (int q = 0; q < R; ++q) {
                             l0 = P::madd(l0, rnew[q], rnew[q]);
                             l1 = P::madd(l1, unew[q], rnew[q]);
                             zm = fmax(zm, fabs(z_[q]));
@@ -244,9 +251,9 @@ __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const 
                 if constexpr (R == 8) fz.eight(it * 8, rs);
                 else rs[0] = fz.one(it);
                 op.rows(kOpST, it, fz, ss);
+                P::rndv(ss);
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    ss[j] = P::rnd(ss[j]);
                     yy[j] = Acc(0);
                     l0 = P::madd(l0, rs[j], rs[j]);
                     l1 = P::madd(l1, ss[j], ss[j]);
@@ -278,11 +285,9 @@ __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const 
                         for (int64_t it = t0; it < items; it += nt) {
                             Acc qq[R];
                             op.rows(kOpS, it, fp, qq);
+                            P::rndv(qq);
 #pragma unroll
-                            for (int j = 0; j < R; ++j) {
-                                qq[j] = P::rnd(qq[j]);
-                                l0 = P::madd(l0, qq[j], qq[j]);
-                            }
+                            for (int j = 0; j < R; ++j) l0 = P::madd(l0, qq[j], qq[j]);
                             IO::st(q, it, qq);
                         }
                     } else {
@@ -293,11 +298,9 @@ __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const 
                             else pp[0] = fp.one(it);
                             IO::st(pn, it, pp);
                             op.rows(kOpS, it, fp, qq);
+                            P::rndv(qq);
 #pragma unroll
-                            for (int j = 0; j < R; ++j) {
-                                qq[j] = P::rnd(qq[j]);
-                                l0 = P::madd(l0, qq[j], qq[j]);
-                            }
+                            for (int j = 0; j < R; ++j) l0 = P::madd(l0, qq[j], qq[j]);
                             IO::st(q, it, qq);
                         }
                     }
@@ -323,9 +326,11 @@ __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const 
                         else rn_[0] = frs.one(it);
                         op.rows(kOpST, it, frs, ss);
 #pragma unroll
+                        for (int j = 0; j < R; ++j) yy[j] = P::madd(yy[j], ac, pp[j]);
+                        P::rndv(yy);
+                        P::rndv(ss);
+#pragma unroll
                         for (int j = 0; j < R; ++j) {
-                            yy[j] = P::rnd(P::madd(yy[j], ac, pp[j]));
-                            ss[j] = P::rnd(ss[j]);
                             l0 = P::madd(l0, rn_[j], rn_[j]);
                             l1 = P::madd(l1, ss[j], ss[j]);
                         }
