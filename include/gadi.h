@@ -201,6 +201,37 @@ GADI_API gadi_status gadi_get_scales(gadi_solver *h, int32_t *sM, int32_t *sN);
 GADI_API gadi_status gadi_predict_params(gadi_solver *h, const double *features, int32_t nfeat,
                                 int32_t kind, double *alpha, double *omega);
 
+/* Allocation-free solve (the paper has no counterpart: this is a library
+ * convenience). Some callers cannot allocate device memory: code that runs
+ * under a fixed memory budget or inside a framework that owns all device
+ * memory through its own pool (where a raw cudaMalloc may fail or fragment
+ * the pool), and latency-critical loops where cudaMalloc's implicit device
+ * synchronisation is not acceptable. gadi_solve_stencil_noalloc serves them:
+ * it solves the constant-coefficient convection-diffusion stencil system of
+ * gadi_stencil (variable_k = 0, HSS splitting, right-hand side b) with
+ * FP16-inner GADI-IR, stopping on eta_inf <= tol, and calls no cudaMalloc,
+ * cudaFree or other allocating routine. No handle is involved.
+ *   dim, N, beta: the operator (as in gadi_stencil); n = N^dim must not
+ *                 exceed GADI_NOALLOC_MAX_N (larger n: GADI_ERR_INVALID_ARG).
+ *   alpha, omega, eps_inner, max_inner, max_outer: as in gadi_set_params and
+ *                 gadi_set_inner.
+ *   b, x:         device (or managed) pointers to n FP64 values, owned by the
+ *                 caller; x holds x0 on entry and the result on return.
+ *   cuda_stream:  stream of the work; the call returns after the result is
+ *                 in x (the stream is synchronised).
+ * Its scratch is one library-owned device array of fixed size (about 7 MB),
+ * present on every GPU that loads the library until the process exits; the
+ * first call on a device looks up that array's address (a one-time set-up
+ * done with the device current) and should come before any stream capture.
+ * Every call uses the same array and leaves its contents behind: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. Returns as gadi_solve. */
+#define GADI_NOALLOC_MAX_N 262144
+GADI_API gadi_status gadi_solve_stencil_noalloc(int32_t dim, int32_t N, double beta, double alpha,
+                                                double omega, double eps_inner, int32_t max_inner,
+                                                int32_t max_outer, const double *b, double *x,
+                                                double tol, void *cuda_stream, gadi_info *info);
+
 /* Release all device memory of h. NULL is accepted. */
 GADI_API void gadi_destroy(gadi_solver *h);
 

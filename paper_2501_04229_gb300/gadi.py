@@ -29,7 +29,7 @@ EXPORTS = [
     "gadi_create", "gadi_set_params", "gadi_set_inner", "gadi_set_stop", "gadi_set_kernel",
     "gadi_set_launch", "gadi_set_wait_limit", "gadi_debug_force_timeout", "gadi_solve",
     "gadi_apply", "gadi_get_scales", "gadi_predict_params", "gadi_destroy", "gadi_status_str",
-    "gadi_last_error",
+    "gadi_last_error", "gadi_solve_stencil_noalloc",
 ]
 
 
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH):
         "gadi_predict_params": (i32, [vp, C.POINTER(f64), i32, i32, C.POINTER(f64), C.POINTER(f64)]),
         "gadi_destroy": (None, [vp]),
         "gadi_status_str": (C.c_char_p, [i32]),
+        "gadi_solve_stencil_noalloc": (i32, [i32, i32, f64, f64, f64, f64, i32, i32, vp, vp, f64, vp,
+                                             C.POINTER(gadi_info)]),
         "gadi_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -215,6 +217,18 @@ def gadi_predict_params(h, features, kind):
     st = load().gadi_predict_params(h, f.ctypes.data_as(C.POINTER(C.c_double)), len(f), int(kind),
                                     C.byref(a), C.byref(w))
     return st, a.value, w.value
+
+
+def gadi_solve_stencil_noalloc(dim, N, beta, alpha, omega, b, x, tol, eps_inner=1e-2,
+                               max_inner=200, max_outer=100000, stream=None):
+    """Allocation-free stencil solve into x (torch CUDA tensors, float64).
+    Returns (status, info dict)."""
+    info = gadi_info()
+    st = load().gadi_solve_stencil_noalloc(int(dim), int(N), float(beta), float(alpha), float(omega),
+                                           float(eps_inner), int(max_inner), int(max_outer),
+                                           C.c_void_p(_ptr(b)), C.c_void_p(_ptr(x)), float(tol),
+                                           C.c_void_p(stream) if stream else None, C.byref(info))
+    return st, info.as_dict()
 
 
 class Solver:
