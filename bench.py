@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--omega", type=float, default=OMEGA)
     ap.add_argument("--kernel", default="stencil", choices=["stencil", "sparse"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GADI comparison")
+    ap.add_argument("--no-spmv", action="store_true", help="skip the operator bandwidth runs")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0,
                     help="bound on the CPU oracle's time for cpu_baseline")
     return ap.parse_args()
@@ -138,6 +139,84 @@ def algorithmic_bytes(n, nnz, info, kernel, fp16):
     return float(vec + mat)
 
 
+def reduce_max(value, world, device="cpu"):
+    """Maximum of a per-rank value over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def kernel_source_digest():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2501_04229_gb300", "csrc", "*.cu*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in txt.splitlines()
+                  if line.startswith(("kernel-source-sha256:", "dram-bytes-per-launch:")))
+    if fields.get("kernel-source-sha256", "").strip() != kernel_source_digest():
+        return None
+    return float(fields["dram-bytes-per-launch"])
+
+
+def apply_bandwidth(G, torch, p, stencil, kernels, flush, stream, reps=10):
+    """GB/s of one H' application per kernel variant: algorithmic bytes (x
+    read once, y written once, matrix bytes as stored per stored entry or per
+    node) over the median CUDA-event time, L2 flushed before each launch."""
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
+    h = G.gadi_create(t(p.A.row_ptr, torch.int32), t(p.A.col_idx, torch.int32), t(p.A.val),
+                      stencil=stencil, stream=stream.cuda_stream)
+    n, nnz = p.n, p.A.nnz
+    out = {}
+    try:
+        for kname, kk in kernels:
+            G.gadi_set_kernel(h, kk)
+            for prec, u_r, dt, vs in (("fp16", G.GADI_F16, torch.float16, 2), ("fp64", G.GADI_F64, torch.float64, 8)):
+                G.gadi_set_params(h, 3.0, 0.0, u_r=u_r)
+                xi = torch.randn(n, device="cuda").to(dt)
+                yo = torch.empty_like(xi)
+                for _ in range(3):
+                    G.gadi_apply(h, G.OP_H, xi, yo)
+                ts = []
+                for _ in range(reps):
+                    flush.fill_(2.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    G.gadi_apply(h, G.OP_H, xi, yo)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1) * 1e-3)
+                if kname == "sparse":
+                    mat = nnz * (vs + 4)
+                elif stencil[3]:
+                    mat = 4 * n * vs            # diagonal + 3 face couplings per node
+                else:
+                    mat = 0
+                byts = 2 * n * vs + mat
+                med = statistics.median(ts)
+                out[f"{p.name}_{kname}_{prec}_H"] = {"GBps": round(byts / med / 1e9, 1), "bytes": byts,
+                                                     "us": round(med * 1e6, 2)}
+    finally:
+        G.gadi_destroy(h)
+    return out
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_2501_04229_gb300 import build as B
@@ -196,11 +275,7 @@ def run_gpu(args, rank, world):
         t16, i16 = timed_solves(args.steps, args.warmup, G.GADI_F16)
     eta_gpu = i16[-1]["eta_inf"]
     x16 = x.cpu().numpy()
-    tot = sum(t16)
-    if world > 1:
-        tt = torch.tensor([tot], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        tot = float(tt.item())
+    tot = reduce_max(sum(t16), world, "cuda")
     ms_per_step = tot / args.steps * 1e3
     kern_t = [i["t_solve_s"] for i in i16]
     info = i16[-1]
@@ -213,30 +288,18 @@ def run_gpu(args, rank, world):
                 "inner_iters_H": i64[-1]["inner_iters_H"], "inner_iters_S": i64[-1]["inner_iters_S"],
                 "eta_inf": i64[-1]["eta_inf"], "eps_inner": EPS64}
 
-    # operator-application bandwidth per variant (L2 flushed before each)
+    # operator-application bandwidth per variant, at sizes where HBM matters
     spmv = {}
-    configure(G.GADI_F16)
-    for kname, kk in (("stencil", G.GADI_KERNEL_STENCIL), ("sparse", G.GADI_KERNEL_SPARSE)):
-        G.gadi_set_kernel(h, kk)
-        for prec, u_r, dt, vs in (("fp16", G.GADI_F16, torch.float16, 2), ("fp64", G.GADI_F64, torch.float64, 8)):
-            G.gadi_set_params(h, args.alpha, args.omega, u_r=u_r)
-            xi = torch.randn(n, device="cuda").to(dt)
-            yo = torch.empty_like(xi)
-            for _ in range(3):
-                G.gadi_apply(h, G.OP_H, xi, yo)
-            ts = []
-            for _ in range(10):
-                flush.fill_(2.0)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                G.gadi_apply(h, G.OP_H, xi, yo)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1) * 1e-3)
-            mat = 0 if kname == "stencil" else nnz * (vs + 4)
-            byts = 2 * n * vs + mat
-            spmv[f"{kname}_{prec}_H"] = {"GBps": round(byts / statistics.median(ts) / 1e9, 1),
-                                         "bytes": byts, "us": round(statistics.median(ts) * 1e6, 2)}
+    if not args.no_spmv:
+        p128 = P.make_problem(3, 128, 50.0, grf_seed=3, name="convdiff3d_128_b50_grf")
+        spmv.update(apply_bandwidth(G, torch, p128, (3, 128, 50.0, 1),
+                                    (("stencil", G.GADI_KERNEL_STENCIL), ("sparse", G.GADI_KERNEL_SPARSE)),
+                                    flush, stream))
+        del p128
+        p192 = P.make_problem(3, 192, 100.0, name="convdiff3d_192_b100")
+        spmv.update(apply_bandwidth(G, torch, p192, (3, 192, 100.0, 0),
+                                    (("stencil", G.GADI_KERNEL_STENCIL),), flush, stream))
+        del p192
     G.gadi_set_kernel(h, kern)
     configure(G.GADI_F16)
 
@@ -268,8 +331,9 @@ def run_gpu(args, rank, world):
         "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(),
         "e2e": statistics.mean(e2e), "roofline": {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None,
-            "kernel": "gadi_solve_kernel<StencilOp<half,3>>" if args.kernel == "stencil"
+            "frac": round(achieved / hbm, 4),
+            "traffic": profiled_traffic("gadi_solve_kernel_convdiff3d_64_b100.md") if args.kernel == "stencil" else None,
+            "kernel": "gadi_solve_kernel<StencilOp<half,3,8>>" if args.kernel == "stencil"
             else "gadi_solve_kernel<EllOp<half>>",
             "note": "whole solve in one persistent launch; the 64^3 working set is L2-resident, so this is an effective rate",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
