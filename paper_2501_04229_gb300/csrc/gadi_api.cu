@@ -524,6 +524,7 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     a.ctl = h->ctl;
     a.part = h->part;
     a.eta_hist = nullptr;
+    a.race_bound = nullptr;
     a.wait_ns = (unsigned long long)(h->wait_ms * 1e6);
     a.extra = h->force_timeout ? 1u : 0u;
 

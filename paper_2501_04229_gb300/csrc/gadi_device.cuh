@@ -227,6 +227,7 @@ struct GridExchange {
     unsigned epoch;
     unsigned long long wait_ns;
     unsigned extra;                // added to the arrival target (never reached: timeout test)
+    bool block_only;               // the team is this block alone (no global memory used)
 
     template <class V, int NS>
     __device__ __forceinline__ bool allreduce(V (&v)[NS], const int (&ops)[NS])
@@ -235,7 +236,7 @@ struct GridExchange {
         V *res = reinterpret_cast<V *>(shd);
         int *s_ok = reinterpret_cast<int *>(shd + 2 * kMaxSlots);
         block_reduce_w0(v, ops);
-        if (gridDim.x == 1) {
+        if (block_only || gridDim.x == 1) {
             if (threadIdx.x == 0)
 #pragma unroll
                 for (int s = 0; s < NS; ++s) res[s] = v[s];

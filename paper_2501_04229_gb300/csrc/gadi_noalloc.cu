@@ -192,6 +192,7 @@ gadi_status launch(int dev, int num_sms, cudaStream_t stream, unsigned char *bas
     a.ctl = ctl;
     a.part = (double *)(base + kCtlBytes);
     a.eta_hist = nullptr;
+    a.race_bound = nullptr;
     a.wait_ns = 2000000000ULL;
     a.extra = 0;
 

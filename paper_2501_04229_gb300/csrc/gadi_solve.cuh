@@ -42,17 +42,25 @@ struct SolveArgs {
     Ctl *ctl;
     double *part;                // [2][kMaxSlots][gridDim] partial sums
     double *eta_hist;            // optional, max_outer + 1 entries
+    const long long *race_bound; // optional (one-block teams): stop once spmv exceeds it
     unsigned long long wait_ns;
     unsigned extra;
 };
+
+// status of a solve stopped by race_bound (reported as not converged)
+constexpr int kRacedOut = 100;
 
 // launch bound: 1024 threads for one-row items, 512 for 8-row items (whose
 // per-thread state is larger)
 template <class Op>
 constexpr int max_threads() { return Op::R == 8 ? 512 : 1024; }
 
+// The solve, run by a team of threads: the whole grid (ex.block_only false,
+// t0/nt the global thread index and count) or one block (ex.block_only true,
+// t0/nt the block's). lead is the one thread that writes the results.
 template <class Op, class T>
-__global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const SolveArgs<Op, T> a)
+__device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchange &ex, const int64_t t0,
+                                           const int64_t nt, const bool lead)
 {
     using P = Prec<T>;
     using Acc = typename P::Acc;
@@ -60,11 +68,7 @@ __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const 
     using IO = ItemIO<T, R>;
     using IO64 = ItemIO64<R>;
     const int64_t items = a.nitems;
-    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
     const Op &op = a.op;
-    GridExchange ex{a.ctl, a.part, 0u, a.wait_ns, a.extra};
-    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const Acc eps2 = (Acc)(a.eps * a.eps);
     const int ops1[1] = {kSum};
     const int ops2[2] = {kSum, kSum};
@@ -112,6 +116,15 @@ __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const 
         if (k == 0) r0 = rn2;
         res = r0 > 0.0 ? rn2 / r0 : 0.0;
         if (lead && a.eta_hist) a.eta_hist[k] = eta;
+        if (a.race_bound) {
+            // one-block teams only: thread 0 reads the bound, the block agrees
+            __shared__ int s_race;
+            if (threadIdx.x == 0) s_race = spmv > *(const volatile long long *)a.race_bound;
+            __syncthreads();
+            const bool raced = s_race != 0;
+            __syncthreads();
+            if (raced) { status = kRacedOut; break; }
+        }
         {
             bool done = true;
             if (!isfinite(rn2) || !isfinite(eta)) status = kErrDiverged;
@@ -383,6 +396,14 @@ __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const 
         c->res = res;
         c->r0 = r0;
     }
+}
+
+template <class Op, class T>
+__global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const SolveArgs<Op, T> a)
+{
+    GridExchange ex{a.ctl, a.part, 0u, a.wait_ns, a.extra, false};
+    solve_body(a, ex, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+               blockIdx.x == 0 && threadIdx.x == 0);
 }
 
 // One operator application y = K x (kernel-level tests, bandwidth runs).

@@ -29,7 +29,7 @@ EXPORTS = [
     "gadi_create", "gadi_set_params", "gadi_set_inner", "gadi_set_stop", "gadi_set_kernel",
     "gadi_set_launch", "gadi_set_wait_limit", "gadi_debug_force_timeout", "gadi_solve",
     "gadi_apply", "gadi_get_scales", "gadi_predict_params", "gadi_destroy", "gadi_status_str",
-    "gadi_last_error", "gadi_solve_stencil_noalloc",
+    "gadi_last_error", "gadi_solve_stencil_noalloc", "gadi_sweep",
 ]
 
 
@@ -53,6 +53,24 @@ class gadi_info(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class gadi_sweep_instance(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("N", C.c_int32), ("beta", C.c_double)]
+
+
+class gadi_sweep_candidate(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("omega", C.c_double)]
+
+
+class gadi_sweep_record(C.Structure):
+    _fields_ = [("instance", C.c_int32), ("candidate", C.c_int32), ("status", C.c_int32),
+                ("raced_out", C.c_int32), ("outer_iters", C.c_int32), ("reserved", C.c_int32),
+                ("inner_iters_H", C.c_int64), ("inner_iters_S", C.c_int64),
+                ("spmv_count", C.c_int64), ("eta_inf", C.c_double), ("time_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class GadiError(RuntimeError):
@@ -93,6 +111,8 @@ def load(path: str = LIB_PATH):
         "gadi_solve_stencil_noalloc": (i32, [i32, i32, f64, f64, f64, f64, i32, i32, vp, vp, f64, vp,
                                              C.POINTER(gadi_info)]),
         "gadi_last_error": (C.c_char_p, [vp]),
+        "gadi_sweep": (i32, [C.POINTER(gadi_sweep_instance), i32, C.POINTER(gadi_sweep_candidate), i32,
+                             f64, f64, i32, i32, i32, i32, vp, C.POINTER(gadi_sweep_record)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -229,6 +249,21 @@ def gadi_solve_stencil_noalloc(dim, N, beta, alpha, omega, b, x, tol, eps_inner=
                                            C.c_void_p(_ptr(b)), C.c_void_p(_ptr(x)), float(tol),
                                            C.c_void_p(stream) if stream else None, C.byref(info))
     return st, info.as_dict()
+
+
+def gadi_sweep(instances, candidates, tol=1e-13, eps_inner=0.1, max_inner=200, max_outer=5000,
+               race=True, block_threads=0, stream=None):
+    """instances: [(dim, N, beta)], candidates: [(alpha, omega)]. Returns a
+    list of record dicts, one per (instance, candidate), instance-major."""
+    ni, nc = len(instances), len(candidates)
+    I = (gadi_sweep_instance * ni)(*[gadi_sweep_instance(int(d), int(N), float(b)) for d, N, b in instances])
+    Cd = (gadi_sweep_candidate * nc)(*[gadi_sweep_candidate(float(a), float(w)) for a, w in candidates])
+    R = (gadi_sweep_record * (ni * nc))()
+    st = load().gadi_sweep(I, ni, Cd, nc, float(tol), float(eps_inner), int(max_inner), int(max_outer),
+                           int(bool(race)), int(block_threads), C.c_void_p(stream) if stream else None, R)
+    if st != GADI_OK:
+        raise GadiError(st, "gadi_sweep failed")
+    return [r.as_dict() for r in R]
 
 
 class Solver:
