@@ -195,11 +195,54 @@ GADI_API gadi_status gadi_apply(gadi_solver *h, int32_t which, const void *x, vo
  * alpha and inner precision. */
 GADI_API gadi_status gadi_get_scales(gadi_solver *h, int32_t *sM, int32_t *sN);
 
-/* Predict (alpha, omega) from problem features (§3.3). features[0] = log n,
- * features[1] = log beta. kind: 0 MLP, 1 GPR, 2 grid search. Returns
- * NO_MODEL when no predictor of that kind has been loaded. */
+/* Predict (alpha, omega) for h's system (§3.3). features[0] = log n,
+ * features[1] = log beta (nfeat >= 2). kind: GADI_MODEL_MLP or
+ * GADI_MODEL_GPR use the model attached with gadi_set_model (NO_MODEL when
+ * none); omega is clamped to [0, 1.999]. GADI_MODEL_GRID searches 16 alpha
+ * (10^-3 .. 10^2) x 4 omega (0, 0.5, 1, 1.5) with solves of h's own system
+ * (b = A 1, x0 = 0, the handle's precisions and inner settings, tol 1e-10),
+ * each capped at the fewest outer steps of a converged candidate so far,
+ * and returns the candidate with the fewest operator applications. */
 GADI_API gadi_status gadi_predict_params(gadi_solver *h, const double *features, int32_t nfeat,
                                 int32_t kind, double *alpha, double *omega);
+
+/* ---- Parameter predictors (§3.3) ------------------------------------------
+ * A model maps features x = (log n, log beta) to targets (log alpha*,
+ * omega*). Both are standardised per column before fitting.
+ *   GADI_MODEL_GPR: Gaussian-process regression (§3.3.1), squared-exponential
+ *     kernel, posterior mean, FP32 arithmetic (the paper fits its GPR in
+ *     FP32), host side. hyper: NULL (length scale and noise chosen by the
+ *     log marginal likelihood on the grid {0.25,0.5,1,2,4} x {1e-3,1e-2,1e-1})
+ *     or {ell, sn}. m <= 4096.
+ *   GADI_MODEL_MLP: 2 -> 64 -> 64 -> 2, tanh, trained on the GPU by full-
+ *     batch Adam on MSE (BF16 weights into tensor-core MMAs, FP32
+ *     accumulation and master weights). hyper: NULL or {epochs [3000],
+ *     lr [1e-2], seed [1]}.
+ * X: m x 2 row-major features; Y: m x 2 targets (host pointers, copied).
+ * The model is owned by the caller (gadi_model_destroy). */
+typedef struct gadi_model gadi_model;
+#define GADI_MODEL_MLP 0
+#define GADI_MODEL_GPR 1
+#define GADI_MODEL_GRID 2
+GADI_API gadi_status gadi_model_fit(int32_t kind, const double *X, const double *Y, int32_t m,
+                                    const double *hyper, int32_t nhyper, void *cuda_stream,
+                                    gadi_model **out);
+/* Y (count x 2) = model(X (count x 2)), host pointers. */
+GADI_API gadi_status gadi_model_predict(const gadi_model *model, const double *X, int32_t count, double *Y);
+/* Training loss per epoch of an MLP (count = epochs; copies min(cap, count)). */
+GADI_API gadi_status gadi_model_loss(const gadi_model *model, double *loss, int32_t cap, int32_t *count);
+/* Gradient of the MLP loss 1/(2m) sum (y - t)^2 at the given parameters on
+ * already standardised X, T (m x 2 each), computed by the training kernels
+ * (BF16 operands, FP32 accumulation). params and grad: gadi_mlp_param_count()
+ * values in the order W1 [64][2], b1 [64], W2 [64][64], b2 [64], W3 [2][64],
+ * b3 [2]. */
+GADI_API gadi_status gadi_mlp_gradient(const double *params, const double *X, const double *T, int32_t m,
+                                       void *cuda_stream, double *grad);
+GADI_API int32_t gadi_mlp_param_count(void);
+GADI_API void gadi_model_destroy(gadi_model *model);
+/* Attach a model (not owned; must outlive its use) to h for
+ * gadi_predict_params of the model's kind. NULL detaches. */
+GADI_API gadi_status gadi_set_model(gadi_solver *h, int32_t kind, const gadi_model *model);
 
 /* ---- Batched parameter sweep --------------------------------------------
  * Many FP16-inner GADI-IR solves in one persistent launch (captured in a

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgadi.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["gadi_api.cu", "gadi_noalloc.cu", "gadi_sweep.cu"]
+SOURCES = ["gadi_api.cu", "gadi_noalloc.cu", "gadi_sweep.cu", "gadi_predict.cu"]
 HEADERS = ["gadi_solve.cuh", "gadi_ops.cuh", "gadi_device.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 FLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",

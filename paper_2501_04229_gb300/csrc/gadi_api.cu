@@ -11,6 +11,7 @@
 #include <new>
 #include <string>
 #include <type_traits>
+#include <vector>
 
 #include "../../include/gadi.h"
 #include "gadi_solve.cuh"
@@ -281,6 +282,7 @@ struct gadi_solver {
     Ctl *ctl = nullptr;
     double *scratch = nullptr;   // small device scratch (norms, flags)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const gadi_model *models[2] = {nullptr, nullptr};   // MLP, GPR (not owned)
     std::string err;
 };
 
@@ -945,12 +947,82 @@ gadi_status gadi_apply(gadi_solver *h, int32_t which, const void *x, void *y)
     });
 }
 
+gadi_status gadi_set_model(gadi_solver *h, int32_t kind, const gadi_model *model)
+{
+    if (!h || (kind != GADI_MODEL_MLP && kind != GADI_MODEL_GPR)) return GADI_ERR_INVALID_ARG;
+    h->models[kind] = model;
+    return GADI_OK;
+}
+
 gadi_status gadi_predict_params(gadi_solver *h, const double *features, int32_t nfeat, int32_t kind,
                                 double *alpha, double *omega)
 {
-    if (!h || !features || nfeat < 1 || !alpha || !omega || kind < 0 || kind > 2)
-        return GADI_ERR_INVALID_ARG;
-    return fail(h, GADI_ERR_NO_MODEL, "no parameter predictor loaded");
+    if (!h || !alpha || !omega || kind < GADI_MODEL_MLP || kind > GADI_MODEL_GRID) return GADI_ERR_INVALID_ARG;
+    if (kind != GADI_MODEL_GRID) {
+        if (!features || nfeat < 2) return fail(h, GADI_ERR_INVALID_ARG, "features need (log n, log beta)");
+        if (!h->models[kind]) return fail(h, GADI_ERR_NO_MODEL, "no model of this kind attached");
+        double y[2];
+        gadi_status st = gadi_model_predict(h->models[kind], features, 1, y);
+        if (st != GADI_OK) return fail(h, st, "model prediction failed");
+        const double a = std::exp(y[0]);
+        if (!(a > 0.0) || !std::isfinite(a)) return fail(h, GADI_ERR_RANGE, "predicted alpha out of range");
+        *alpha = a;
+        *omega = std::min(1.999, std::max(0.0, y[1]));
+        return GADI_OK;
+    }
+    // grid search on the handle's own system: b = A 1, x0 = 0, each candidate
+    // capped at the fewest outer steps of a converged candidate so far
+    const int64_t n = h->n;
+    double *ones = nullptr, *b = nullptr, *x = nullptr;
+    auto cleanup = [&]() {
+        if (ones) cudaFree(ones);
+        if (b) cudaFree(b);
+        if (x) cudaFree(x);
+    };
+    if (dalloc(&ones, n) || dalloc(&b, n) || dalloc(&x, n)) {
+        cudaGetLastError();
+        cleanup();
+        return fail(h, GADI_ERR_OUT_OF_MEMORY, "grid search buffers");
+    }
+    std::vector<double> h1(n, 1.0);
+    cudaError_t e = cudaMemcpyAsync(ones, h1.data(), n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) { cleanup(); return fail(h, GADI_ERR_CUDA, "grid search upload"); }
+    const double save_a = h->alpha, save_w = h->omega;
+    const int save_outer = h->max_outer;
+    gadi_status st = gadi_apply(h, kOpA, ones, b);
+    if (st != GADI_OK) { cleanup(); return st; }
+    long long best_cost = -1;
+    int best_outer = save_outer;
+    double ba = 0, bw = 0;
+    for (int ia = 0; ia < 16; ++ia)
+        for (int iw = 0; iw < 4; ++iw) {
+            const double a = std::pow(10.0, -3.0 + 5.0 * ia / 15.0), w = 0.5 * iw;
+            h->alpha = a;
+            h->omega = w;
+            h->max_outer = best_outer;
+            if ((e = cudaMemsetAsync(x, 0, n * sizeof(double), h->stream)) != cudaSuccess) break;
+            gadi_info info;
+            gadi_status s2 = gadi_solve(h, b, x, 1e-10, &info);
+            if (s2 == GADI_ERR_CUDA || s2 == GADI_ERR_OUT_OF_MEMORY || s2 == GADI_ERR_TIMEOUT) { st = s2; break; }
+            if (s2 != GADI_OK) continue;
+            if (best_cost < 0 || info.spmv_count < best_cost) {
+                best_cost = info.spmv_count;
+                best_outer = std::min(best_outer, info.outer_iters);
+                ba = a;
+                bw = w;
+            }
+        }
+    h->alpha = save_a;
+    h->omega = save_w;
+    h->max_outer = save_outer;
+    h->demoted = false;
+    cleanup();
+    if (e != cudaSuccess) return fail(h, GADI_ERR_CUDA, "grid search");
+    if (st != GADI_OK) return st;
+    if (best_cost < 0) return fail(h, GADI_ERR_NOT_CONVERGED, "no grid candidate converged");
+    *alpha = ba;
+    *omega = bw;
+    return GADI_OK;
 }
 
 }  // extern "C"

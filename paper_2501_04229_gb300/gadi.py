@@ -29,8 +29,11 @@ EXPORTS = [
     "gadi_create", "gadi_set_params", "gadi_set_inner", "gadi_set_stop", "gadi_set_kernel",
     "gadi_set_launch", "gadi_set_wait_limit", "gadi_debug_force_timeout", "gadi_solve",
     "gadi_apply", "gadi_get_scales", "gadi_predict_params", "gadi_destroy", "gadi_status_str",
-    "gadi_last_error", "gadi_solve_stencil_noalloc", "gadi_sweep",
+    "gadi_last_error", "gadi_solve_stencil_noalloc", "gadi_sweep", "gadi_model_fit",
+    "gadi_model_predict", "gadi_model_loss", "gadi_mlp_gradient", "gadi_mlp_param_count",
+    "gadi_model_destroy", "gadi_set_model",
 ]
+GADI_MODEL_MLP, GADI_MODEL_GPR, GADI_MODEL_GRID = 0, 1, 2
 
 
 class gadi_csr(C.Structure):
@@ -113,6 +116,13 @@ def load(path: str = LIB_PATH):
         "gadi_last_error": (C.c_char_p, [vp]),
         "gadi_sweep": (i32, [C.POINTER(gadi_sweep_instance), i32, C.POINTER(gadi_sweep_candidate), i32,
                              f64, f64, i32, i32, i32, i32, vp, C.POINTER(gadi_sweep_record)]),
+        "gadi_model_fit": (i32, [i32, vp, vp, i32, vp, i32, vp, C.POINTER(vp)]),
+        "gadi_model_predict": (i32, [vp, vp, i32, vp]),
+        "gadi_model_loss": (i32, [vp, vp, i32, C.POINTER(i32)]),
+        "gadi_mlp_gradient": (i32, [vp, vp, vp, i32, vp, vp]),
+        "gadi_mlp_param_count": (i32, []),
+        "gadi_model_destroy": (None, [vp]),
+        "gadi_set_model": (i32, [vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -232,7 +242,7 @@ def gadi_get_scales(h):
 
 
 def gadi_predict_params(h, features, kind):
-    f = np.ascontiguousarray(features, dtype=np.float64)
+    f = np.ascontiguousarray(features if features is not None else [0.0, 0.0], dtype=np.float64)
     a, w = C.c_double(), C.c_double()
     st = load().gadi_predict_params(h, f.ctypes.data_as(C.POINTER(C.c_double)), len(f), int(kind),
                                     C.byref(a), C.byref(w))
@@ -264,6 +274,63 @@ def gadi_sweep(instances, candidates, tol=1e-13, eps_inner=0.1, max_inner=200, m
     if st != GADI_OK:
         raise GadiError(st, "gadi_sweep failed")
     return [r.as_dict() for r in R]
+
+
+def _f64c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def gadi_model_fit(kind, X, Y, hyper=None, stream=None):
+    """Fit a predictor (GADI_MODEL_MLP or GADI_MODEL_GPR) on X (m x 2
+    features) and Y (m x 2 targets); returns the model handle."""
+    X, Y = _f64c(X), _f64c(Y)
+    h = None if hyper is None else _f64c(hyper)
+    m = C.c_void_p()
+    st = load().gadi_model_fit(int(kind), X.ctypes.data, Y.ctypes.data, len(X),
+                               None if h is None else h.ctypes.data, 0 if h is None else len(h),
+                               C.c_void_p(stream) if stream else None, C.byref(m))
+    if st != GADI_OK:
+        raise GadiError(st, "gadi_model_fit failed")
+    return m
+
+
+def gadi_model_predict(model, X):
+    X = _f64c(X)
+    Y = np.empty((len(X), 2))
+    st = load().gadi_model_predict(model, X.ctypes.data, len(X), Y.ctypes.data)
+    if st != GADI_OK:
+        raise GadiError(st, "gadi_model_predict failed")
+    return Y
+
+
+def gadi_model_loss(model):
+    cnt = C.c_int32()
+    load().gadi_model_loss(model, None, 0, C.byref(cnt))
+    out = np.empty(max(cnt.value, 1))
+    load().gadi_model_loss(model, out.ctypes.data, cnt.value, C.byref(cnt))
+    return out[:cnt.value]
+
+
+def gadi_mlp_gradient(params, X, T, stream=None):
+    params, X, T = _f64c(params), _f64c(X), _f64c(T)
+    g = np.empty(load().gadi_mlp_param_count())
+    st = load().gadi_mlp_gradient(params.ctypes.data, X.ctypes.data, T.ctypes.data, len(X),
+                                  C.c_void_p(stream) if stream else None, g.ctypes.data)
+    if st != GADI_OK:
+        raise GadiError(st, "gadi_mlp_gradient failed")
+    return g
+
+
+def gadi_mlp_param_count():
+    return int(load().gadi_mlp_param_count())
+
+
+def gadi_model_destroy(model):
+    load().gadi_model_destroy(model)
+
+
+def gadi_set_model(h, kind, model):
+    _check(h, load().gadi_set_model(h, int(kind), model))
 
 
 class Solver:
