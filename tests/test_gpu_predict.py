@@ -79,7 +79,7 @@ def test_mlp_initial_loss_matches_oracle():
         G.gadi_model_destroy(m)
 
 
-@pytest.mark.parametrize("hyper", [[0.5, 1e-2], [2.0, 1e-3], None])
+@pytest.mark.parametrize("hyper", [[0.5, 1e-2], [0.5, 1e-3], [1.0, 3e-2], None])
 def test_gpr_matches_oracle(hyper):
     rng = np.random.default_rng(2)
     X = np.stack([rng.uniform(5, 14, 30), rng.uniform(-2, 7, 30)], axis=1)
