@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--alpha", type=float, default=ALPHA)
     ap.add_argument("--omega", type=float, default=OMEGA)
     ap.add_argument("--kernel", default="stencil", choices=["stencil", "sparse"])
+    ap.add_argument("--params", default="mlp", choices=["mlp", "gpr", "fixed"],
+                    help="(alpha, omega): predicted by the MLP or GPR trained on a sweep of small "
+                         "3D systems (untimed set-up), or the fixed --alpha/--omega")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GADI comparison")
     ap.add_argument("--no-spmv", action="store_true", help="skip the operator bandwidth runs")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0,
@@ -217,6 +220,36 @@ def apply_bandwidth(G, torch, p, stencil, kernels, flush, stream, reps=10):
     return out
 
 
+def learned_params(G, workload_n, workload_beta):
+    """Training records from a batched sweep of small 3D systems of the same
+    structure (sides 8..48, 5 convection strengths, 12 alpha x 3 omega), then
+    the MLP (trained on the GPU) and the GPR; their (alpha, omega) for the
+    workload's (log n, log beta)."""
+    from paper_2501_04229_gb300 import sweep as SW
+    inst = [(3, N, b) for N in (8, 16, 24, 32, 40, 48) for b in (2.0, 10.0, 40.0, 100.0, 300.0)]
+    cands = SW.candidates(n_alpha=12, omegas=(0.0, 0.5, 1.0), lo=-1.0, hi=1.5)
+    t0 = time.perf_counter()
+    recs = SW.run(inst, cands=cands, eps_inner=EPS16, max_outer=4000)
+    t_sweep = time.perf_counter() - t0
+    rows = [r for r in recs if r["best"]]
+    X = np.array([[r["log_n"], r["log_beta"]] for r in rows])
+    Y = np.array([[math.log(r["best"]["alpha"]), r["best"]["omega"]] for r in rows])
+    q = np.array([[math.log(workload_n), math.log(workload_beta)]])
+    out = {"train_instances": len(rows), "candidates": len(cands), "sweep_s": round(t_sweep, 3)}
+    t0 = time.perf_counter()
+    mlp = G.gadi_model_fit(G.GADI_MODEL_MLP, X, Y, hyper=[3000, 1e-2, 1])
+    out["mlp_train_s"] = round(time.perf_counter() - t0, 3)
+    gpr = G.gadi_model_fit(G.GADI_MODEL_GPR, X, Y)
+    try:
+        for name, m in (("mlp", mlp), ("gpr", gpr)):
+            y = G.gadi_model_predict(m, q)[0]
+            out[name] = {"alpha": float(math.exp(y[0])), "omega": float(min(1.999, max(0.0, y[1])))}
+    finally:
+        G.gadi_model_destroy(mlp)
+        G.gadi_model_destroy(gpr)
+    return out
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_2501_04229_gb300 import build as B
@@ -237,6 +270,11 @@ def run_gpu(args, rank, world):
     b = t(p.b)
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    predictor = None
+    if args.params != "fixed":
+        predictor = learned_params(G, n, p.beta)
+        args.alpha = predictor[args.params]["alpha"]
+        args.omega = predictor[args.params]["omega"]
 
     def configure(u_r):
         G.gadi_set_params(h, args.alpha, args.omega, u_r=u_r)
@@ -248,6 +286,13 @@ def run_gpu(args, rank, world):
         for _ in range(w):
             x.zero_()
             st, info = G.gadi_solve(h, b, x, TOL)
+            if st != G.GADI_OK and args.params != "fixed" and predictor is not None:
+                # predicted parameters failed: fall back to the fixed pair
+                predictor["fallback"] = {"status": G.status_str(st), "alpha": ALPHA, "omega": OMEGA}
+                args.alpha, args.omega, args.params = ALPHA, OMEGA, "fixed"
+                configure(u_r)
+                x.zero_()
+                st, info = G.gadi_solve(h, b, x, TOL)
             assert st == G.GADI_OK, G.last_error(h)
         times, infos = [], []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -329,7 +374,7 @@ def run_gpu(args, rank, world):
     return {
         "ms_per_step": ms_per_step, "value": tot / args.steps, "info": info, "eta_gpu": eta_gpu,
         "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(),
-        "e2e": statistics.mean(e2e), "roofline": {
+        "e2e": statistics.mean(e2e), "predictor": predictor, "roofline": {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4),
             "traffic": profiled_traffic("gadi_solve_kernel_convdiff3d_64_b100.md") if args.kernel == "stencil" else None,
@@ -375,7 +420,7 @@ def main():
             "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "data": "synthetic (3D convection-diffusion, manufactured solution)"}
     cfg = {"workload": WORKLOAD, "n": 262144, "nnz": 1810432, "beta": 100.0, "tol_eta_inf": TOL,
-           "alpha": args.alpha, "omega": args.omega, "eps_inner": EPS16,
+           "params": args.params, "eps_inner": EPS16,
            "precisions": "u_r=fp16 (fp32 arithmetic), u=u_f=fp64", "kernel": args.kernel,
            "l2": "flushed before every timed step (256 MB write)",
            "parallelism": "replicas" if world > 1 else "single GPU"}
@@ -426,6 +471,8 @@ def main():
         "solve": {k: r["info"][k] for k in ("outer_iters", "inner_iters_H", "inner_iters_S", "spmv_count",
                                             "grid_blocks", "block_threads")},
         "eta_inf_gpu": r["eta_gpu"], "eta_inf_oracle_check": eta_cpu, "max_abs_err_vs_exact": fwd,
+        "params_used": {"source": args.params, "alpha": args.alpha, "omega": args.omega},
+        "predictor": r["predictor"],
         "fp64_gadi_same_gpu": r["fp64"],
         "speedup_vs_fp64_gadi": (r["fp64"]["time_s"] / r["value"]) if r["fp64"] else None,
         "spmv": r["spmv"],
