@@ -155,10 +155,20 @@ GADI_API gadi_status gadi_set_stop(gadi_solver *h, gadi_stop kind);
  * returns INVALID_ARG. */
 GADI_API gadi_status gadi_set_kernel(gadi_solver *h, gadi_kernel kind);
 
+/* Rows per work item of the stencil kernels (an implementation choice, not
+ * part of the paper's method: operator applications are bit-identical for
+ * every value; the dot products of a solve sum in another order):
+ * 0 = automatic (8 when the grid side N is a multiple of 8, else 4 when a
+ * multiple of 4, else 1), or 1, 4, 8 -- used when N is a multiple of it,
+ * else 1. An item of R rows is R consecutive nodes of one x-line, read with
+ * one 2R-byte FP16 load per vector. Other values return INVALID_ARG. */
+GADI_API gadi_status gadi_set_item_rows(gadi_solver *h, int32_t rows);
+
 /* Launch shape of the persistent solve kernel: grid_blocks (0 = automatic,
  * else 1 .. the co-resident maximum) and block_threads (0 = automatic, else
  * 128, 256, 512 or 1024). One block runs the solve with block-local barriers
- * only. */
+ * only. gadi_apply uses the same shape when set (else one item per thread,
+ * 256 threads per block). */
 GADI_API gadi_status gadi_set_launch(gadi_solver *h, int32_t grid_blocks, int32_t block_threads);
 
 /* Upper bound, in milliseconds, of every device-side grid-barrier wait

@@ -267,6 +267,7 @@ struct gadi_solver {
     int max_inner = 200, max_outer = 100000;
     int stop = GADI_STOP_ETA;
     int kernel = GADI_KERNEL_AUTO;
+    int item_rows = 0;        // stencil rows per item: 0 = automatic, 1, 4 or 8
     int blocks = 0, threads = 0;
     double wait_ms = 2000.0;
     int force_timeout = 0;
@@ -574,7 +575,10 @@ gadi_status run_apply(gadi_solver *h, int which, const void *x, void *y)
     if constexpr (std::is_same<Op, EllOp<T>>::value) op = make_ell<T>(h);
     else op = make_stencil<T, Op::kDim, Op::R>(h);
     const int64_t nitems = h->n / Op::R;
-    gadi_apply_kernel<Op, T><<<grid_for(nitems), kSetupThreads, 0, h->stream>>>(op, nitems, which, x, y);
+    // launch shape: gadi_set_launch's when given, else one item per thread
+    const int threads = h->threads ? h->threads : kSetupThreads;
+    const unsigned blocks = h->blocks ? (unsigned)h->blocks : grid_for(nitems, threads);
+    gadi_apply_kernel<Op, T><<<blocks, threads, 0, h->stream>>>(op, nitems, which, x, y);
     CK(cudaGetLastError());
     return GADI_OK;
 }
@@ -584,17 +588,37 @@ struct Tag {
     using type = X;
 };
 
+// stencil rows per item in use: the one set by gadi_set_item_rows when the
+// grid side is a multiple of it, else 8 or 4 when the side allows, else 1
+int item_rows(const gadi_solver *h)
+{
+    if (h->item_rows > 0 && h->sN % h->item_rows == 0) return h->item_rows;
+    if (h->item_rows == 0) {
+        if (h->sN % 8 == 0) return 8;
+        if (h->sN % 4 == 0) return 4;
+    }
+    return 1;
+}
+
 // call fn(Tag<Op>, Tag<T>) with the operator family and inner type in use:
-// the sparse operator, or the stencil for dim 2/3 with 8-row items when
-// the grid side is a multiple of 8
+// the sparse operator, or the stencil for dim 2/3 with items of 1, 4 or 8
+// rows of one grid line
+template <class T, int DIM, class Fn>
+gadi_status dispatch_rows(const gadi_solver *h, Fn &&fn)
+{
+    switch (item_rows(h)) {
+    case 8: return fn(Tag<StencilOp<T, DIM, 8>>{}, Tag<T>{});
+    case 4: return fn(Tag<StencilOp<T, DIM, 4>>{}, Tag<T>{});
+    default: return fn(Tag<StencilOp<T, DIM, 1>>{}, Tag<T>{});
+    }
+}
+
 template <class T, class Fn>
 gadi_status dispatch_op(const gadi_solver *h, Fn &&fn)
 {
     if (!use_stencil(h)) return fn(Tag<EllOp<T>>{}, Tag<T>{});
-    const bool v8 = h->sN % 8 == 0;
-    if (h->sdim == 3)
-        return v8 ? fn(Tag<StencilOp<T, 3, 8>>{}, Tag<T>{}) : fn(Tag<StencilOp<T, 3, 1>>{}, Tag<T>{});
-    return v8 ? fn(Tag<StencilOp<T, 2, 8>>{}, Tag<T>{}) : fn(Tag<StencilOp<T, 2, 1>>{}, Tag<T>{});
+    if (h->sdim == 3) return dispatch_rows<T, 3>(h, fn);
+    return dispatch_rows<T, 2>(h, fn);
 }
 
 template <class Fn>
@@ -848,6 +872,15 @@ gadi_status gadi_set_kernel(gadi_solver *h, gadi_kernel kind)
     if (kind == GADI_KERNEL_STENCIL && !h->has_stencil)
         return fail(h, GADI_ERR_INVALID_ARG, "the stencil kernels need a stencil descriptor at create");
     h->kernel = kind;
+    return GADI_OK;
+}
+
+gadi_status gadi_set_item_rows(gadi_solver *h, int32_t rows)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (rows != 0 && rows != 1 && rows != 4 && rows != 8)
+        return fail(h, GADI_ERR_INVALID_ARG, "rows per item must be 0 (automatic), 1, 4 or 8");
+    h->item_rows = rows;
     return GADI_OK;
 }
 

@@ -7,8 +7,9 @@
 //   kOpST : (S'^T x)_i                    (CGNR's transpose product)
 //
 // Work is done in items of R consecutive rows (R = 1 for the general sparse
-// operator, R = 8 for the stencil when the grid side is a multiple of 8:
-// one 16-byte FP16 load per vector and one coordinate computation per item).
+// operator; R = 4 or 8 for the stencil when the grid side is a multiple of
+// R: one 8- or 16-byte FP16 load per vector and one coordinate computation
+// per item).
 //
 // A row is evaluated as sigma*f(i) first, then the matrix entries in
 // ascending column order (the CSR order). Inner precision FP16: products of
@@ -17,7 +18,7 @@
 // So a row equals, bit for bit, the same sum formed on the CPU.
 //
 // The vector argument is an expression object with one(j) (value at column
-// j) and eight(j0, out) (values at j0..j0+7, j0 a multiple of 8); the kernel
+// j) and many<K>(j0, out) (values at j0..j0+K-1, j0 a multiple of K); the kernel
 // passes expressions such as "r + beta p rounded to FP16" so that vector
 // updates of a Krylov step fuse into the next operator application.
 #pragma once
@@ -29,45 +30,70 @@ namespace gadi {
 enum : int { kOpA = 0, kOpH = 1, kOpS = 2, kOpST = 3 };
 
 // ---------------------------------------------------------------------------
-// 8-wide loads and stores of FP16 / FP64 vectors (16-byte transactions)
+// K-wide loads and stores of FP16 / FP64 vectors (K = 4 or 8; one 8- or
+// 16-byte transaction per FP16 chunk)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void ld8(const __half *p, int64_t j0, float (&o)[8])
+template <int K>
+__device__ __forceinline__ void ldv(const __half *p, int64_t j0, float (&o)[K])
 {
-    const uint4 u = *reinterpret_cast<const uint4 *>(p + j0);
-    const __half2 *h = reinterpret_cast<const __half2 *>(&u);
+    static_assert(K == 4 || K == 8, "chunk width");
+    if constexpr (K == 8) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(p + j0);
+        const __half2 *h = reinterpret_cast<const __half2 *>(&u);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        float2 f = __half22float2(h[k]);
-        o[2 * k] = f.x;
-        o[2 * k + 1] = f.y;
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __half22float2(h[k]);
+            o[2 * k] = f.x;
+            o[2 * k + 1] = f.y;
+        }
+    } else {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p + j0);
+        const __half2 *h = reinterpret_cast<const __half2 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float2 f = __half22float2(h[k]);
+            o[2 * k] = f.x;
+            o[2 * k + 1] = f.y;
+        }
     }
 }
 
-__device__ __forceinline__ void st8(__half *p, int64_t j0, const float (&v)[8])
+template <int K>
+__device__ __forceinline__ void stv(__half *p, int64_t j0, const float (&v)[K])
 {
-    uint4 u;
-    __half2 *h = reinterpret_cast<__half2 *>(&u);
+    if constexpr (K == 8) {
+        uint4 u;
+        __half2 *h = reinterpret_cast<__half2 *>(&u);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) h[k] = __float22half2_rn(make_float2(v[2 * k], v[2 * k + 1]));
-    *reinterpret_cast<uint4 *>(p + j0) = u;
+        for (int k = 0; k < 4; ++k) h[k] = __float22half2_rn(make_float2(v[2 * k], v[2 * k + 1]));
+        *reinterpret_cast<uint4 *>(p + j0) = u;
+    } else {
+        uint2 u;
+        __half2 *h = reinterpret_cast<__half2 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) h[k] = __float22half2_rn(make_float2(v[2 * k], v[2 * k + 1]));
+        *reinterpret_cast<uint2 *>(p + j0) = u;
+    }
 }
 
-__device__ __forceinline__ void ld8(const double *p, int64_t j0, double (&o)[8])
+template <int K>
+__device__ __forceinline__ void ldv(const double *p, int64_t j0, double (&o)[K])
 {
     const double2 *q = reinterpret_cast<const double2 *>(p + j0);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        double2 d = q[k];
+    for (int k = 0; k < K / 2; ++k) {
+        const double2 d = q[k];
         o[2 * k] = d.x;
         o[2 * k + 1] = d.y;
     }
 }
 
-__device__ __forceinline__ void st8(double *p, int64_t j0, const double (&v)[8])
+template <int K>
+__device__ __forceinline__ void stv(double *p, int64_t j0, const double (&v)[K])
 {
     double2 *q = reinterpret_cast<double2 *>(p + j0);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) q[k] = make_double2(v[2 * k], v[2 * k + 1]);
+    for (int k = 0; k < K / 2; ++k) q[k] = make_double2(v[2 * k], v[2 * k + 1]);
 }
 
 // own-row access of an item of R rows; values rounded to T on store
@@ -76,12 +102,12 @@ struct ItemIO {
     using Acc = typename Prec<T>::Acc;
     static __device__ __forceinline__ void ld(const T *p, int64_t item, Acc (&o)[R])
     {
-        if constexpr (R == 8) ld8(p, item * 8, o);
+        if constexpr (R > 1) ldv<R>(p, item * R, o);
         else o[0] = Prec<T>::ld(p[item]);
     }
     static __device__ __forceinline__ void st(T *p, int64_t item, const Acc (&v)[R])
     {
-        if constexpr (R == 8) st8(p, item * 8, v);
+        if constexpr (R > 1) stv<R>(p, item * R, v);
         else p[item] = Prec<T>::st(v[0]);
     }
 };
@@ -90,12 +116,12 @@ template <int R>
 struct ItemIO64 {
     static __device__ __forceinline__ void ld(const double *p, int64_t item, double (&o)[R])
     {
-        if constexpr (R == 8) ld8(p, item * 8, o);
+        if constexpr (R > 1) ldv<R>(p, item * R, o);
         else o[0] = p[item];
     }
     static __device__ __forceinline__ void st(double *p, int64_t item, const double (&v)[R])
     {
-        if constexpr (R == 8) st8(p, item * 8, v);
+        if constexpr (R > 1) stv<R>(p, item * R, v);
         else p[item] = v[0];
     }
 };
@@ -108,7 +134,8 @@ struct XLoad {                       // a
     using Acc = typename Prec<T>::Acc;
     const T *a;
     __device__ __forceinline__ Acc one(int64_t j) const { return Prec<T>::ld(a[j]); }
-    __device__ __forceinline__ void eight(int64_t j0, Acc (&o)[8]) const { ld8(a, j0, o); }
+    template <int K>
+    __device__ __forceinline__ void many(int64_t j0, Acc (&o)[K]) const { ldv<K>(a, j0, o); }
 };
 
 template <class T>
@@ -118,13 +145,14 @@ struct XAxpy {                       // fl(a + c b)
     const T *a, *b;
     Acc c;
     __device__ __forceinline__ Acc one(int64_t j) const { return P::rnd(P::madd(P::ld(a[j]), c, P::ld(b[j]))); }
-    __device__ __forceinline__ void eight(int64_t j0, Acc (&o)[8]) const
+    template <int K>
+    __device__ __forceinline__ void many(int64_t j0, Acc (&o)[K]) const
     {
-        Acc x[8], y[8];
-        ld8(a, j0, x);
-        ld8(b, j0, y);
+        Acc x[K], y[K];
+        ldv<K>(a, j0, x);
+        ldv<K>(b, j0, y);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = P::madd(x[k], c, y[k]);
+        for (int k = 0; k < K; ++k) o[k] = P::madd(x[k], c, y[k]);
         P::rndv(o);
     }
 };
@@ -140,17 +168,18 @@ struct XAxpy2 {                      // fl(a - c fl(b + d e))  (C-G residual upd
         const Acc s = P::rnd(P::madd(P::ld(b[j]), d, P::ld(e[j])));
         return P::rnd(P::madd(P::ld(a[j]), -c, s));
     }
-    __device__ __forceinline__ void eight(int64_t j0, Acc (&o)[8]) const
+    template <int K>
+    __device__ __forceinline__ void many(int64_t j0, Acc (&o)[K]) const
     {
-        Acc x[8], y[8], w[8];
-        ld8(a, j0, x);
-        ld8(b, j0, y);
-        ld8(e, j0, w);
+        Acc x[K], y[K], w[K];
+        ldv<K>(a, j0, x);
+        ldv<K>(b, j0, y);
+        ldv<K>(e, j0, w);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) w[k] = P::madd(y[k], d, w[k]);
+        for (int k = 0; k < K; ++k) w[k] = P::madd(y[k], d, w[k]);
         P::rndv(w);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = P::madd(x[k], -c, w[k]);
+        for (int k = 0; k < K; ++k) o[k] = P::madd(x[k], -c, w[k]);
         P::rndv(o);
     }
 };
@@ -162,12 +191,13 @@ struct XScale {                      // fl(c a), c a power of two
     const T *a;
     Acc c;
     __device__ __forceinline__ Acc one(int64_t j) const { return P::rnd(P::mul(P::ld(a[j]), c)); }
-    __device__ __forceinline__ void eight(int64_t j0, Acc (&o)[8]) const
+    template <int K>
+    __device__ __forceinline__ void many(int64_t j0, Acc (&o)[K]) const
     {
-        Acc x[8];
-        ld8(a, j0, x);
+        Acc x[K];
+        ldv<K>(a, j0, x);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = P::mul(x[k], c);
+        for (int k = 0; k < K; ++k) o[k] = P::mul(x[k], c);
         P::rndv(o);
     }
 };
@@ -178,19 +208,21 @@ struct XDemote {                     // fl_T(2^-e r), r in FP64 (Alg. 1: r^ = fl
     const double *r;
     double sc;
     __device__ __forceinline__ Acc one(int64_t j) const { return Prec<T>::ld(Prec<T>::from64(r[j] * sc)); }
-    __device__ __forceinline__ void eight(int64_t j0, Acc (&o)[8]) const
+    template <int K>
+    __device__ __forceinline__ void many(int64_t j0, Acc (&o)[K]) const
     {
-        double x[8];
-        ld8(r, j0, x);
+        double x[K];
+        ldv<K>(r, j0, x);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = Prec<T>::ld(Prec<T>::from64(x[k] * sc));
+        for (int k = 0; k < K; ++k) o[k] = Prec<T>::ld(Prec<T>::from64(x[k] * sc));
     }
 };
 
 struct XLoad64 {
     const double *a;
     __device__ __forceinline__ double one(int64_t j) const { return a[j]; }
-    __device__ __forceinline__ void eight(int64_t j0, double (&o)[8]) const { ld8(a, j0, o); }
+    template <int K>
+    __device__ __forceinline__ void many(int64_t j0, double (&o)[K]) const { ldv<K>(a, j0, o); }
 };
 
 // ---------------------------------------------------------------------------
@@ -244,7 +276,7 @@ struct EllOp {
 
 // ---------------------------------------------------------------------------
 // Matrix-free 5-point (2D) / 7-point (3D) convection-diffusion operator of
-// §4.1 on an N^dim grid, x fastest; R = 8 needs N % 8 == 0 (an item is 8
+// §4.1 on an N^dim grid, x fastest; R > 1 needs N % R == 0 (an item is R
 // nodes of one x-line). Constant-k form: scalar coefficients. Face form:
 // per-node arrays of the diagonal and of the upper-face couplings per axis
 // (M is symmetric, so the lower coupling of node i along d is the upper
@@ -342,8 +374,8 @@ struct StencilOp {
         return acc;
     }
 
-    // ---- 8-row items (R == 8) -----------------------------------------------
-    // Items of 8: neighbours along y and z are whole aligned chunks; along x
+    // ---- R-row items (R = 4 or 8) ----------------------------------------------
+    // Items of R: neighbours along y and z are whole aligned chunks; along x
     // they are the item's own values shifted by one, with the two ends from
     // one().
     template <class F>
@@ -352,50 +384,50 @@ struct StencilOp {
         if constexpr (R == 1) {
             out[0] = rowA1(item, f);
         } else {
-            const int64_t i0 = item * 8;
+            const int64_t i0 = item * R;
             unsigned cd[3];
             coords(i0, cd);
             const unsigned last = (unsigned)N - 1;
             const bool face = AD != nullptr;
-            double c[8], acc[8], t[8], cf[8];
+            double c[R], acc[R], t[R], cf[R];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = 0.0;
-            f.eight(i0, c);
+            for (int k = 0; k < R; ++k) acc[k] = 0.0;
+            f.template many<R>(i0, c);
 #pragma unroll
             for (int d = DIM - 1; d >= 1; --d)
                 if (cd[d] > 0) {
-                    f.eight(i0 - stride(d), t);
-                    if (face) ld8(AL[d], i0, cf);
+                    f.template many<R>(i0 - stride(d), t);
+                    if (face) ldv<R>(AL[d], i0, cf);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(face ? cf[k] : a_lo, t[k], acc[k]);
+                    for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_lo, t[k], acc[k]);
                 }
             {   // x lower
                 const double xm = cd[0] > 0 ? f.one(i0 - 1) : 0.0;
-                if (face) ld8(AL[0], i0, cf);
+                if (face) ldv<R>(AL[0], i0, cf);
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
+                for (int k = 0; k < R; ++k)
                     if (k > 0 || cd[0] > 0) acc[k] = __fma_rn(face ? cf[k] : a_lo, k ? c[k - 1] : xm, acc[k]);
             }
-            if (face) ld8(AD, i0, cf);
+            if (face) ldv<R>(AD, i0, cf);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(face ? cf[k] : a_diag, c[k], acc[k]);
+            for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_diag, c[k], acc[k]);
             {   // x upper
-                const double xp = cd[0] + 8 <= last ? f.one(i0 + 8) : 0.0;
-                if (face) ld8(AU[0], i0, cf);
+                const double xp = cd[0] + R <= last ? f.one(i0 + R) : 0.0;
+                if (face) ldv<R>(AU[0], i0, cf);
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (k < 7 || cd[0] + 8 <= last) acc[k] = __fma_rn(face ? cf[k] : a_hi, k < 7 ? c[k + 1] : xp, acc[k]);
+                for (int k = 0; k < R; ++k)
+                    if (k < R - 1 || cd[0] + R <= last) acc[k] = __fma_rn(face ? cf[k] : a_hi, k < R - 1 ? c[k + 1] : xp, acc[k]);
             }
 #pragma unroll
             for (int d = 1; d < DIM; ++d)
                 if (cd[d] < last) {
-                    f.eight(i0 + stride(d), t);
-                    if (face) ld8(AU[d], i0, cf);
+                    f.template many<R>(i0 + stride(d), t);
+                    if (face) ldv<R>(AU[d], i0, cf);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(face ? cf[k] : a_hi, t[k], acc[k]);
+                    for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_hi, t[k], acc[k]);
                 }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) out[k] = acc[k];
+            for (int k = 0; k < R; ++k) out[k] = acc[k];
         }
     }
 
@@ -406,93 +438,93 @@ struct StencilOp {
         if constexpr (R == 1) {
             out[0] = row1(which, item, f);
         } else {
-            const int64_t i0 = item * 8;
+            const int64_t i0 = item * R;
             unsigned cd[3];
             coords(i0, cd);
             const unsigned last = (unsigned)N - 1;
-            Acc c[8], acc[8], t[8], cf[8];
-            f.eight(i0, c);
+            Acc c[R], acc[R], t[R], cf[R];
+            f.template many<R>(i0, c);
             if (which == kOpH) {
                 const bool face = HD != nullptr;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) acc[k] = P::mul(sigH, c[k]);
+                for (int k = 0; k < R; ++k) acc[k] = P::mul(sigH, c[k]);
 #pragma unroll
                 for (int d = DIM - 1; d >= 1; --d)
                     if (cd[d] > 0) {
-                        f.eight(i0 - stride(d), t);
-                        if (face) ld8(HK[d], i0 - stride(d), cf);
+                        f.template many<R>(i0 - stride(d), t);
+                        if (face) ldv<R>(HK[d], i0 - stride(d), cf);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], face ? cf[k] : h_off, t[k]);
+                        for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], face ? cf[k] : h_off, t[k]);
                     }
                 {   // x lower: coupling of node i with i-1 is HK[0][i-1]
                     const Acc xm = cd[0] > 0 ? f.one(i0 - 1) : Acc(0);
                     Acc c0 = h_off;
                     if (face) {
-                        ld8(HK[0], i0, cf);
+                        ldv<R>(HK[0], i0, cf);
                         c0 = cd[0] > 0 ? P::ld(HK[0][i0 - 1]) : Acc(0);
                     }
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
+                    for (int k = 0; k < R; ++k)
                         if (k > 0 || cd[0] > 0)
                             acc[k] = P::madd(acc[k], face ? (k ? cf[k - 1] : c0) : h_off, k ? c[k - 1] : xm);
                 }
                 if (face) {
-                    Acc dg[8];
-                    ld8(HD, i0, dg);
+                    Acc dg[R];
+                    ldv<R>(HD, i0, dg);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], dg[k], c[k]);
+                    for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], dg[k], c[k]);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], h_diag, c[k]);
+                    for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], h_diag, c[k]);
                 }
                 {   // x upper: coupling HK[0][i]
-                    const Acc xp = cd[0] + 8 <= last ? f.one(i0 + 8) : Acc(0);
+                    const Acc xp = cd[0] + R <= last ? f.one(i0 + R) : Acc(0);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (k < 7 || cd[0] + 8 <= last)
-                            acc[k] = P::madd(acc[k], face ? cf[k] : h_off, k < 7 ? c[k + 1] : xp);
+                    for (int k = 0; k < R; ++k)
+                        if (k < R - 1 || cd[0] + R <= last)
+                            acc[k] = P::madd(acc[k], face ? cf[k] : h_off, k < R - 1 ? c[k + 1] : xp);
                 }
 #pragma unroll
                 for (int d = 1; d < DIM; ++d)
                     if (cd[d] < last) {
-                        f.eight(i0 + stride(d), t);
-                        if (face) ld8(HK[d], i0, cf);
+                        f.template many<R>(i0 + stride(d), t);
+                        if (face) ldv<R>(HK[d], i0, cf);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], face ? cf[k] : h_off, t[k]);
+                        for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], face ? cf[k] : h_off, t[k]);
                     }
             } else {
                 const Acc lo = which == kOpS ? -s_c : s_c;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) acc[k] = P::mul(sigS, c[k]);
+                for (int k = 0; k < R; ++k) acc[k] = P::mul(sigS, c[k]);
 #pragma unroll
                 for (int d = DIM - 1; d >= 1; --d)
                     if (cd[d] > 0) {
-                        f.eight(i0 - stride(d), t);
+                        f.template many<R>(i0 - stride(d), t);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], lo, t[k]);
+                        for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], lo, t[k]);
                     }
                 {
                     const Acc xm = cd[0] > 0 ? f.one(i0 - 1) : Acc(0);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
+                    for (int k = 0; k < R; ++k)
                         if (k > 0 || cd[0] > 0) acc[k] = P::madd(acc[k], lo, k ? c[k - 1] : xm);
                 }
                 {
-                    const Acc xp = cd[0] + 8 <= last ? f.one(i0 + 8) : Acc(0);
+                    const Acc xp = cd[0] + R <= last ? f.one(i0 + R) : Acc(0);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (k < 7 || cd[0] + 8 <= last) acc[k] = P::madd(acc[k], -lo, k < 7 ? c[k + 1] : xp);
+                    for (int k = 0; k < R; ++k)
+                        if (k < R - 1 || cd[0] + R <= last) acc[k] = P::madd(acc[k], -lo, k < R - 1 ? c[k + 1] : xp);
                 }
 #pragma unroll
                 for (int d = 1; d < DIM; ++d)
                     if (cd[d] < last) {
-                        f.eight(i0 + stride(d), t);
+                        f.template many<R>(i0 + stride(d), t);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) acc[k] = P::madd(acc[k], -lo, t[k]);
+                        for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], -lo, t[k]);
                     }
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) out[k] = acc[k];
+            for (int k = 0; k < R; ++k) out[k] = acc[k];
         }
     }
 };

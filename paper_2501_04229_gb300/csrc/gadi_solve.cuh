@@ -50,10 +50,10 @@ struct SolveArgs {
 // status of a solve stopped by race_bound (reported as not converged)
 constexpr int kRacedOut = 100;
 
-// launch bound: 1024 threads for one-row items, 512 for 8-row items (whose
-// per-thread state is larger)
+// launch bound: 1024 threads for one-row items, 512 for 4- and 8-row items
+// (whose per-thread state is larger)
 template <class Op>
-constexpr int max_threads() { return Op::R == 8 ? 512 : 1024; }
+constexpr int max_threads() { return Op::R > 1 ? 512 : 1024; }
 
 // The solve, run by a team of threads: the whole grid (ex.block_only false,
 // t0/nt the global thread index and count) or one block (ex.block_only true,
@@ -150,7 +150,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
             for (int64_t it = t0; it < items; it += nt) {
                 Acc rr[R], uu[R], zz[R];
                 op.rows(kOpH, it, fr, uu);
-                if constexpr (R == 8) fr.eight(it * 8, rr);
+                if constexpr (R > 1) fr.template many<R>(it * R, rr);
                 else rr[0] = fr.one(it);
                 P::rndv(uu);
 #pragma unroll
@@ -261,7 +261,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
             Acc l0 = 0, l1 = 0;
             for (int64_t it = t0; it < items; it += nt) {
                 Acc rs[R], ss[R], yy[R];
-                if constexpr (R == 8) fz.eight(it * 8, rs);
+                if constexpr (R > 1) fz.template many<R>(it * R, rs);
                 else rs[0] = fz.one(it);
                 op.rows(kOpST, it, fz, ss);
                 P::rndv(ss);
@@ -307,7 +307,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
                         const XAxpy<T> fp{s, pc, be};
                         for (int64_t it = t0; it < items; it += nt) {
                             Acc pp[R], qq[R];
-                            if constexpr (R == 8) fp.eight(it * 8, pp);
+                            if constexpr (R > 1) fp.template many<R>(it * R, pp);
                             else pp[0] = fp.one(it);
                             IO::st(pn, it, pp);
                             op.rows(kOpS, it, fp, qq);
@@ -335,7 +335,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
                         Acc yy[R], pp[R], rn_[R], ss[R];
                         IO::ld(y, it, yy);
                         IO::ld(pc, it, pp);
-                        if constexpr (R == 8) frs.eight(it * 8, rn_);
+                        if constexpr (R > 1) frs.template many<R>(it * R, rn_);
                         else rn_[0] = frs.one(it);
                         op.rows(kOpST, it, frs, ss);
 #pragma unroll

@@ -89,10 +89,11 @@ __host__ __device__ inline double row_norm_hd(int dim, int N, double lo, double 
 
 struct XOnes64 {
     __device__ __forceinline__ double one(int64_t) const { return 1.0; }
-    __device__ __forceinline__ void eight(int64_t, double (&o)[8]) const
+    template <int K>
+    __device__ __forceinline__ void many(int64_t, double (&o)[K]) const
     {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = 1.0;
+        for (int k = 0; k < K; ++k) o[k] = 1.0;
     }
 };
 

@@ -104,6 +104,46 @@ def test_apply_bit_exact(name, kernel, u_r, alpha):
         G.gadi_destroy(h)
 
 
+ROWS_PROBLEMS = {
+    "3d_16_b40": lambda: P.make_problem(3, 16, 40.0),
+    "3d_16_b30_grf": lambda: P.make_problem(3, 16, 30.0, grf_seed=5),
+    "2d_40_b20": lambda: P.make_problem(2, 40, 20.0, rhs="ones"),
+    "3d_12_b50_grf": lambda: P.make_problem(3, 12, 50.0, grf_seed=3),
+}
+
+
+@pytest.mark.parametrize("name", list(ROWS_PROBLEMS))
+@pytest.mark.parametrize("rows", [1, 4, 8])
+@pytest.mark.parametrize("u_r", [G.GADI_F16, G.GADI_F64])
+def test_apply_item_rows_bit_exact(name, rows, u_r):
+    """Stencil items of 1, 4 and 8 rows of a grid line give the oracle's
+    application bit for bit (N = 12 is not a multiple of 8: rows 8 falls back
+    to single rows there)."""
+    p = ROWS_PROBLEMS[name]()
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 0.37, 1.0, u_r=u_r)
+        G.gadi_set_kernel(h, G.GADI_KERNEL_STENCIL)
+        G.gadi_set_item_rows(h, rows)
+        prec = oracle.PREC_HALF if u_r == G.GADI_F16 else oracle.PREC_DOUBLE
+        tdt = torch.float16 if u_r == G.GADI_F16 else torch.float64
+        for which in (G.OP_A, G.OP_H, G.OP_S, G.OP_ST):
+            x = _half_vector(p.n, 30 + which) if (which != G.OP_A and u_r == G.GADI_F16) \
+                else P.random_vector(p.n, 40 + which)
+            want, _, _ = oracle.lp_apply(p.A, 0.37, which, prec, x)
+            xd = _dev(x, torch.float64 if which == G.OP_A else tdt)
+            yd = torch.empty_like(xd)
+            G.gadi_apply(h, which, xd, yd)
+            torch.cuda.synchronize()
+            got = yd.double().cpu().numpy()
+            if p.faces is not None and u_r == G.GADI_F64 and which in (G.OP_S, G.OP_ST):
+                assert np.allclose(got, want, rtol=1e-14, atol=1e-15 * np.abs(want).max())
+            else:
+                assert np.array_equal(got, want), (which, np.abs(got - want).max())
+    finally:
+        G.gadi_destroy(h)
+
+
 def test_apply_user_split_bit_exact():
     p = P.make_problem(3, 9, 30.0)
     m_hss, _ = oracle.hss_split(p.A)
@@ -216,6 +256,30 @@ def test_user_split_solve_matches_oracle():
         G.gadi_destroy(h)
 
 
+@pytest.mark.parametrize("rows", [1, 4, 8])
+@pytest.mark.parametrize("u_r", [G.GADI_F16, G.GADI_F64])
+def test_item_rows_solve_matches_oracle(rows, u_r):
+    p = ROWS_PROBLEMS["3d_16_b40"]()
+    prec = oracle.PREC_HALF if u_r == G.GADI_F16 else oracle.PREC_DOUBLE
+    eps = 1e-2 if u_r == G.GADI_F16 else 1e-10
+    want, oinfo, _ = oracle.gadi_ir(p.A, p.b, 2.5, 0.5, tol=1e-13, eps_inner=eps, prec=prec, max_outer=5000)
+    assert oinfo["status"] == oracle.OK
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 2.5, 0.5, u_r=u_r)
+        G.gadi_set_inner(h, eps, 200, 5000)
+        G.gadi_set_kernel(h, G.GADI_KERNEL_STENCIL)
+        G.gadi_set_item_rows(h, rows)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK, G.last_error(h)
+        assert oracle.backward_error(p.A, p.b, x) <= 1e-13
+        assert np.linalg.norm(x - want) <= 1e-9 * np.linalg.norm(want)
+        slack = 0.15 if u_r == G.GADI_F16 else 0.0
+        assert abs(info["outer_iters"] - oinfo["outer_iters"]) <= max(1, slack * oinfo["outer_iters"])
+    finally:
+        G.gadi_destroy(h)
+
+
 @pytest.mark.parametrize("blocks,threads", [(1, 1024), (3, 128), (16, 256), (0, 0)])
 def test_launch_shapes_agree(blocks, threads):
     """Single-block and multi-block (grid-barrier) launches of the persistent
@@ -307,6 +371,10 @@ def test_invalid_arguments_rejected():
         assert (x == 7.0).all()
         with pytest.raises(G.GadiError):
             G.gadi_solve(h, b, x.cpu().numpy(), 1e-10)
+        for rows in (-1, 2, 3, 16):
+            with pytest.raises(G.GadiError) as e:
+                G.gadi_set_item_rows(h, rows)
+            assert e.value.status == G.GADI_ERR_INVALID_ARG
     finally:
         G.gadi_destroy(h)
     # structurally unsymmetric pattern, unsorted columns, stencil mismatch
@@ -351,3 +419,68 @@ def test_predictor_without_model():
         assert st == G.GADI_ERR_NO_MODEL
     finally:
         G.gadi_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# full-size workload and degenerate cases
+# ---------------------------------------------------------------------------
+
+def test_full_size_64cubed_workload_against_oracle():
+    """The bench workload (64^3, beta = 100, manufactured solution) at full
+    size, in the bench's launch configuration: eta recomputed by the oracle,
+    the solution against the oracle's FP64-inner GADI-IR solution and against
+    the manufactured one (forward error <= kappa * eta, kappa(A) < 2e3 here)."""
+    p = P.workload("convdiff3d_64_b100")
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 3.0, 0.0)
+        G.gadi_set_inner(h, 0.1, 500, 100000)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK
+    finally:
+        G.gadi_destroy(h)
+    assert oracle.backward_error(p.A, p.b, x) <= 1e-13
+    want, oinfo, _ = oracle.gadi_ir(p.A, p.b, 3.0, 0.0, tol=1e-13, eps_inner=0.1,
+                                    prec=oracle.PREC_DOUBLE, max_inner=500, max_outer=5000)
+    assert oinfo["status"] == oracle.OK
+    assert np.linalg.norm(x - want) <= 1e-9 * np.linalg.norm(want)
+    # A is positive real with symmetric part M: ||x - u_h||_2 <= ||r||_2 / lambda_min(M),
+    # lambda_min(M) = 3 (2 - 2 cos(pi h)) for the k = 1 operator (plus the rounding of b)
+    lam = 3 * (2 - 2 * np.cos(np.pi / 65))
+    rn = np.linalg.norm(oracle.residual(p.A, p.b, x))
+    assert np.linalg.norm(x - p.x_exact) <= rn / lam + 1e-11
+
+
+def test_pure_diffusion_beta_zero():
+    """beta = 0: N = 0, S = alpha I, so every CGNR solve takes one iteration."""
+    p = P.make_problem(3, 16, 0.0)
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 0.5, 1.0)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK
+        assert info["inner_iters_S"] == info["outer_iters"]
+        assert oracle.backward_error(p.A, p.b, x) <= 1e-13
+    finally:
+        G.gadi_destroy(h)
+
+
+def test_omega_near_two_still_converges():
+    """Thm 1 allows any omega in [0, 2); close to 2 the update (2 - omega) a
+    is small and convergence slow, but it converges."""
+    p = P.make_problem(2, 16, 5.0)
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 1.0, 1.9)
+        G.gadi_set_inner(h, 0.1, 200, 100000)
+        st, info, x = _solve(h, p, 1e-12)
+        assert st == G.GADI_OK
+        assert oracle.backward_error(p.A, p.b, x) <= 1e-12
+    finally:
+        G.gadi_destroy(h)
+
+
+def test_empty_system_rejected():
+    with pytest.raises(G.GadiError) as e:
+        G.gadi_create(np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    assert e.value.status == G.GADI_ERR_INVALID_ARG
