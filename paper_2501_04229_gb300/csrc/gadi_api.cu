@@ -277,7 +277,8 @@ struct gadi_solver {
     double demoted_alpha = 0.0;
     // work
     double *bdev = nullptr, *xdev = nullptr, *r64 = nullptr;
-    void *vec = nullptr;      // 9 vectors of n elements of the inner type (sized for FP64)
+    void *vec = nullptr;      // 9 vectors of n elements of the inner type (sized for FP64);
+                              // with FP16 inner vectors, the FP32 residual copy follows them
     double *part = nullptr;
     int part_blocks = 0;
     Ctl *ctl = nullptr;
@@ -317,6 +318,19 @@ template <class X>
 cudaError_t dalloc(X **p, size_t count)
 {
     return cudaMalloc((void **)p, (count ? count : 1) * sizeof(X));
+}
+
+// the inner work vectors (9 n FP64, or 9 n FP16 followed by the n-float
+// round-to-odd residual copy at a 256-byte boundary)
+size_t vec_bytes(int64_t n)
+{
+    const size_t half_path = ((size_t)9 * n * sizeof(__half) + 255) / 256 * 256 + (size_t)n * sizeof(float);
+    return std::max((size_t)9 * n * sizeof(double), half_path);
+}
+
+float *r32_of(void *vec, int64_t n)
+{
+    return reinterpret_cast<float *>(static_cast<char *>(vec) + ((size_t)9 * n * sizeof(__half) + 255) / 256 * 256);
 }
 
 void release(gadi_solver *h)
@@ -512,6 +526,7 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     a.b = b;
     a.x = x;
     a.r64 = h->r64;
+    a.r32 = r32_of(h->vec, n);
     for (int j = 0; j < 9; ++j) a.v[j] = V + j * n;
     a.anorm = h->anorm;
     a.bnorm = bnorm;
@@ -812,7 +827,7 @@ gadi_status gadi_create(const gadi_csr *A, gadi_splitting split, const gadi_csr 
             }
         }
         if (dalloc(&h->r64, n) || dalloc(&h->bdev, n) || dalloc(&h->xdev, n) ||
-            cudaMalloc(&h->vec, (size_t)9 * n * sizeof(double)) || dalloc(&h->ctl, 1)) {
+            cudaMalloc(&h->vec, vec_bytes(n)) || dalloc(&h->ctl, 1)) {
             cudaGetLastError();
             return bail(GADI_ERR_OUT_OF_MEMORY);
         }

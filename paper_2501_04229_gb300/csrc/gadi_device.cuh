@@ -4,6 +4,8 @@
 #pragma once
 
 #include <cuda_fp16.h>
+
+#include "gadi_bits.cuh"
 #include <stdint.h>
 
 namespace gadi {
@@ -31,6 +33,8 @@ template <> struct Prec<__half> {
     // round an Acc value through the storage type
     static __device__ __forceinline__ float rnd(float v) { return __half2float(__float2half_rn(v)); }
     static __device__ __forceinline__ __half from64(double v) { return __double2half(v); }
+    // the exact FP64 value of an FP32 value, by integer operations
+    static __device__ __forceinline__ double to64(float v) { return double_of_float(v); }
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
@@ -60,6 +64,7 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double st(double v) { return v; }
     static __device__ __forceinline__ double rnd(double v) { return v; }
     static __device__ __forceinline__ double from64(double v) { return v; }
+    static __device__ __forceinline__ double to64(double v) { return v; }
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }

@@ -77,6 +77,28 @@ __device__ __forceinline__ void stv(__half *p, int64_t j0, const float (&v)[K])
 }
 
 template <int K>
+__device__ __forceinline__ void ldv(const float *p, int64_t j0, float (&o)[K])
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p + j0);
+#pragma unroll
+    for (int k = 0; k < K / 4; ++k) {
+        const float4 d = q[k];
+        o[4 * k] = d.x;
+        o[4 * k + 1] = d.y;
+        o[4 * k + 2] = d.z;
+        o[4 * k + 3] = d.w;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void stv(float *p, int64_t j0, const float (&v)[K])
+{
+    float4 *q = reinterpret_cast<float4 *>(p + j0);
+#pragma unroll
+    for (int k = 0; k < K / 4; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+
+template <int K>
 __device__ __forceinline__ void ldv(const double *p, int64_t j0, double (&o)[K])
 {
     const double2 *q = reinterpret_cast<const double2 *>(p + j0);
@@ -206,15 +228,42 @@ template <class T>
 struct XDemote {                     // fl_T(2^-e r), r in FP64 (Alg. 1: r^ = fl_r(s^))
     using Acc = typename Prec<T>::Acc;
     const double *r;
-    double sc;
-    __device__ __forceinline__ Acc one(int64_t j) const { return Prec<T>::ld(Prec<T>::from64(r[j] * sc)); }
+    double sc;                       // 2^-e
+    __device__ __forceinline__ Acc one(int64_t j) const
+    {
+        return Prec<T>::ld(Prec<T>::from64(sc == 1.0 ? r[j] : r[j] * sc));
+    }
     template <int K>
     __device__ __forceinline__ void many(int64_t j0, Acc (&o)[K]) const
     {
         double x[K];
         ldv<K>(r, j0, x);
 #pragma unroll
-        for (int k = 0; k < K; ++k) o[k] = Prec<T>::ld(Prec<T>::from64(x[k] * sc));
+        for (int k = 0; k < K; ++k) o[k] = Prec<T>::ld(Prec<T>::from64(sc == 1.0 ? x[k] : x[k] * sc));
+    }
+};
+
+// fl16(2^-e r) from the round-to-odd FP32 copy of r: an exact FP32 scaling
+// and one round-to-nearest-even conversion give the same FP16 value as the
+// direct conversion from FP64 (valid for -100 <= e <= 126, where entries
+// below the FP32 normal range round to zero either way)
+struct XDemoteOdd {
+    const float *r32;
+    float sc;                        // 2^-e
+    __device__ __forceinline__ float one(int64_t j) const
+    {
+        return __half2float(__float2half_rn(__fmul_rn(r32[j], sc)));
+    }
+    template <int K>
+    __device__ __forceinline__ void many(int64_t j0, float (&o)[K]) const
+    {
+        float x[K];
+        ldv<K>(r32, j0, x);
+#pragma unroll
+        for (int k = 0; k < K; ++k) x[k] = __fmul_rn(x[k], sc);
+        Prec<__half>::rndv(x);
+#pragma unroll
+        for (int k = 0; k < K; ++k) o[k] = x[k];
     }
 };
 

@@ -24,6 +24,8 @@
 // same way.
 #pragma once
 
+#include <type_traits>
+
 #include "gadi_ops.cuh"
 
 namespace gadi {
@@ -35,6 +37,7 @@ struct SolveArgs {
     const double *b;
     double *x;
     double *r64;
+    float *r32;                  // n floats: round-to-odd copy of r (FP16 inner path)
     T *v[9];                     // inner work vectors, n elements each
     double anorm, bnorm, tol, eps, pfac;
     int sM, sN, half, stop_kind;
@@ -100,6 +103,13 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
                     xmax = fmax(xmax, fabs(xx[q]));
                 }
                 IO64::st(a.r64, it, rr);
+                if constexpr (std::is_same<T, __half>::value) {
+                    float ro[R];
+#pragma unroll
+                    for (int q = 0; q < R; ++q) ro[q] = __uint_as_float(float_bits_round_odd(rr[q]));
+                    if constexpr (R > 1) stv<R>(a.r32, it * R, ro);
+                    else a.r32[it] = ro[0];
+                }
             }
             vR[0] = lsum;
             vR[1] = lmax;
@@ -144,8 +154,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
         T *rc = a.v[0], *rn = a.v[1], *uc = a.v[2], *un = a.v[3];
         T *sc = a.v[4], *sn = a.v[5], *p = a.v[6];
         Acc g[2] = {0, 0};
-        {
-            const XDemote<T> fr{a.r64, ldexp(1.0, -e)};
+        auto d_pass = [&](const auto &fr) {
             Acc l0 = 0, l1 = 0;
             for (int64_t it = t0; it < items; it += nt) {
                 Acc rr[R], uu[R], zz[R];
@@ -165,6 +174,13 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
             }
             g[0] = l0;
             g[1] = l1;
+        };
+        if constexpr (std::is_same<T, __half>::value) {
+            // from the round-to-odd FP32 copy where that is exact, else from FP64
+            if (e >= -100 && e <= 126) d_pass(XDemoteOdd{a.r32, ldexpf(1.0f, -e)});
+            else d_pass(XDemote<T>{a.r64, ldexp(1.0, -e)});
+        } else {
+            d_pass(XDemote<T>{a.r64, ldexp(1.0, -e)});
         }
         if (!ex.allreduce(g, ops2)) return;
         ++spmv;
@@ -378,7 +394,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
                 IO64::ld(a.x, it, xx);
                 IO::ld(y, it, yy);
 #pragma unroll
-                for (int j = 0; j < R; ++j) xx[j] = __fma_rn(upd, (double)yy[j], xx[j]);
+                for (int j = 0; j < R; ++j) xx[j] = __fma_rn(upd, P::to64(yy[j]), xx[j]);
                 IO64::st(a.x, it, xx);
             }
         }
