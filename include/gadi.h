@@ -314,7 +314,7 @@ GADI_API gadi_status gadi_sweep(const gadi_sweep_instance *instances, int32_t ni
  *                 caller; x holds x0 on entry and the result on return.
  *   cuda_stream:  stream of the work; the call returns after the result is
  *                 in x (the stream is synchronised).
- * Its scratch is one library-owned device array of fixed size (about 7.5 MB),
+ * Its scratch is one library-owned device array of fixed size (about 9.5 MB),
  * present on every GPU that loads the library until the process exits; the
  * first call on a device looks up that array's address (a one-time set-up
  * done with the device current) and should come before any stream capture.

@@ -277,6 +277,7 @@ struct gadi_solver {
     double demoted_alpha = 0.0;
     // work
     double *bdev = nullptr, *xdev = nullptr, *r64 = nullptr;
+    double *x2 = nullptr;     // second iterate buffer (the iterates alternate with x)
     void *vec = nullptr;      // 9 vectors of n elements of the inner type (sized for FP64);
                               // with FP16 inner vectors, the FP32 residual copy follows them
     double *part = nullptr;
@@ -338,7 +339,7 @@ void release(gadi_solver *h)
     void *ptrs[] = {h->ecol, h->ea, h->em, h->en, h->ent, h->m16, h->n16, h->nt16, h->AD,
                     h->AL[0], h->AL[1], h->AL[2], h->AU[0], h->AU[1], h->AU[2], h->HD64,
                     h->HK64[0], h->HK64[1], h->HK64[2], h->HD16, h->HK16[0], h->HK16[1],
-                    h->HK16[2], h->bdev, h->xdev, h->r64, h->vec, h->part, h->ctl, h->scratch};
+                    h->HK16[2], h->bdev, h->xdev, h->x2, h->r64, h->vec, h->part, h->ctl, h->scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -525,6 +526,7 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     a.nitems = nitems;
     a.b = b;
     a.x = x;
+    a.x2 = h->x2;
     a.r64 = h->r64;
     a.r32 = r32_of(h->vec, n);
     for (int j = 0; j < 9; ++j) a.v[j] = V + j * n;
@@ -826,7 +828,7 @@ gadi_status gadi_create(const gadi_csr *A, gadi_splitting split, const gadi_csr 
                 h->a_hi = h->a_lo = h->m_off = h->n_up = 0.0;
             }
         }
-        if (dalloc(&h->r64, n) || dalloc(&h->bdev, n) || dalloc(&h->xdev, n) ||
+        if (dalloc(&h->r64, n) || dalloc(&h->bdev, n) || dalloc(&h->xdev, n) || dalloc(&h->x2, n) ||
             cudaMalloc(&h->vec, vec_bytes(n)) || dalloc(&h->ctl, 1)) {
             cudaGetLastError();
             return bail(GADI_ERR_OUT_OF_MEMORY);

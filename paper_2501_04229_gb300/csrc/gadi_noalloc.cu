@@ -1,7 +1,8 @@
 // gadi_noalloc.cu -- gadi_solve_stencil_noalloc: a GADI-IR solve of the
 // constant-coefficient convection-diffusion stencil that allocates no device
 // memory. Its scratch (control block, reduction partials, FP64 residual, its
-// FP32 copy and the FP16 inner vectors) lives in one file-scope __device__ array of fixed
+// FP32 copy, a second iterate and the FP16 inner vectors) lives in one
+// file-scope __device__ array of fixed
 // size, g_noalloc_scratch, which every GPU that loads the library holds until
 // the process exits.
 //
@@ -30,8 +31,9 @@ constexpr size_t kPartBytes = (size_t)2 * kMaxSlots * kNoallocMaxBlocks * sizeof
 constexpr size_t kChkBytes = 256;
 constexpr size_t kR64Bytes = (size_t)kNoallocMaxN * sizeof(double);
 constexpr size_t kR32Bytes = (size_t)kNoallocMaxN * sizeof(float);
+constexpr size_t kX2Bytes = (size_t)kNoallocMaxN * sizeof(double);
 constexpr size_t kVecBytes = (size_t)9 * kNoallocMaxN * sizeof(__half);
-constexpr size_t kScratchBytes = kCtlBytes + kPartBytes + kChkBytes + kR64Bytes + kR32Bytes + kVecBytes;
+constexpr size_t kScratchBytes = kCtlBytes + kPartBytes + kChkBytes + kR64Bytes + kR32Bytes + kX2Bytes + kVecBytes;
 
 }  // namespace
 
@@ -178,7 +180,8 @@ gadi_status launch(int dev, int num_sms, cudaStream_t stream, unsigned char *bas
     a.x = x;
     a.r64 = (double *)(base + kCtlBytes + kPartBytes + kChkBytes);
     a.r32 = (float *)(base + kCtlBytes + kPartBytes + kChkBytes + kR64Bytes);
-    __half *V = (__half *)(base + kCtlBytes + kPartBytes + kChkBytes + kR64Bytes + kR32Bytes);
+    a.x2 = (double *)(base + kCtlBytes + kPartBytes + kChkBytes + kR64Bytes + kR32Bytes);
+    __half *V = (__half *)(base + kCtlBytes + kPartBytes + kChkBytes + kR64Bytes + kR32Bytes + kX2Bytes);
     for (int j = 0; j < 9; ++j) a.v[j] = V + j * n;
     a.anorm = anorm;
     a.bnorm = bnorm;

@@ -35,7 +35,8 @@ struct SolveArgs {
     Op op;
     int64_t n, nitems;
     const double *b;
-    double *x;
+    double *x;                   // in: x0, out: the result
+    double *x2;                  // n doubles: the iterates alternate between x and x2
     double *r64;
     float *r32;                  // n floats: round-to-odd copy of r (FP16 inner path)
     T *v[9];                     // inner work vectors, n elements each
@@ -83,18 +84,19 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
     double r0 = 0.0, best = INFINITY, eta = 0.0, res = 0.0;
     long long itH = 0, itS = 0, spmv = 0;
     int k = 0, status = kErrNotConverged;
+    double *xcur = a.x;              // the buffer holding the current iterate
 
     for (;;) {
         // ---- R: outer residual in FP64 -----------------------------------------
         double vR[3] = {0.0, 0.0, 0.0};
         {
             double lmax = 0.0, lsum = 0.0, xmax = 0.0;
-            const XLoad64 fx{a.x};
+            const XLoad64 fx{xcur};
             for (int64_t it = t0; it < items; it += nt) {
                 double ax[R], bb[R], xx[R], rr[R];
                 op.rowsA(it, fx, ax);
                 IO64::ld(a.b, it, bb);
-                IO64::ld(a.x, it, xx);
+                IO64::ld(xcur, it, xx);
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
                     rr[q] = __dsub_rn(bb[q], ax[q]);
@@ -299,6 +301,12 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
         const Acc rr0s = c0[0];
 
         // ---- CGNR on S' ----------------------------------------------------------
+        // Every B pass also forms the candidate update (Alg. 1 step 4, FP64)
+        //   x_next = x + (2-w) a 2^(e - sM + ez - sN) y
+        // for its own rows; after the last pass x_next is the new iterate, so
+        // no separate update pass and grid synchronisation are needed.
+        const double upd = ldexp(a.pfac, e - a.sM + ez - a.sN);
+        double *const xnext = xcur == a.x ? a.x2 : a.x;
         int it_s = 0;
         if (rr0s > Acc(0)) {
             ++spmv;
@@ -349,8 +357,10 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
                     Acc l0 = 0, l1 = 0;
                     for (int64_t it = t0; it < items; it += nt) {
                         Acc yy[R], pp[R], rn_[R], ss[R];
+                        double xx[R];
                         IO::ld(y, it, yy);
                         IO::ld(pc, it, pp);
+                        IO64::ld(xcur, it, xx);
                         if constexpr (R > 1) frs.template many<R>(it * R, rn_);
                         else rn_[0] = frs.one(it);
                         op.rows(kOpST, it, frs, ss);
@@ -358,6 +368,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
                         for (int j = 0; j < R; ++j) yy[j] = P::madd(yy[j], ac, pp[j]);
                         P::rndv(yy);
                         P::rndv(ss);
+#pragma unroll
+                        for (int j = 0; j < R; ++j) xx[j] = __fma_rn(upd, P::to64(yy[j]), xx[j]);
+                        IO64::st(xnext, it, xx);
 #pragma unroll
                         for (int j = 0; j < R; ++j) {
                             l0 = P::madd(l0, rn_[j], rn_[j]);
@@ -382,25 +395,19 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
                 first = false;
             }
             if (status == kErrDiverged) break;
+            xcur = xnext;            // (no CGNR step: y = 0 and x stays)
         }
         itS += it_s;
 
-        // ---- U: x += (2-w) a 2^(e - sM + ez - sN) y (FP64) ------------------------
-        {
-            const double upd = ldexp(a.pfac, e - a.sM + ez - a.sN);
-            for (int64_t it = t0; it < items; it += nt) {
-                double xx[R];
-                Acc yy[R];
-                IO64::ld(a.x, it, xx);
-                IO::ld(y, it, yy);
-#pragma unroll
-                for (int j = 0; j < R; ++j) xx[j] = __fma_rn(upd, P::to64(yy[j]), xx[j]);
-                IO64::st(a.x, it, xx);
-            }
-        }
-        if (!ex.sync()) return;
         ++k;
     }
+    // the result belongs in x: copy the own items when the last iterate is in x2
+    if (xcur != a.x)
+        for (int64_t it = t0; it < items; it += nt) {
+            double xx[R];
+            IO64::ld(xcur, it, xx);
+            IO64::st(a.x, it, xx);
+        }
     if (lead) {
         Ctl *c = a.ctl;
         c->status = status;

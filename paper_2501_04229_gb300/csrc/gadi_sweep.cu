@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(512, 1) gadi_sweep_kernel(const SweepArgs s)
     double *bvec = reinterpret_cast<double *>(mine + 256);
     double *xvec = bvec + s.maxn;
     double *r64 = xvec + s.maxn;
-    float *r32 = reinterpret_cast<float *>(r64 + s.maxn);
+    double *x2 = r64 + s.maxn;
+    float *r32 = reinterpret_cast<float *>(x2 + s.maxn);
     __half *V = reinterpret_cast<__half *>(r32 + s.maxn);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(s.next, 1);
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(512, 1) gadi_sweep_kernel(const SweepArgs s)
         a.nitems = nitems;
         a.b = bvec;
         a.x = xvec;
+        a.x2 = x2;
         a.r64 = r64;
         a.r32 = r32;
         for (int j = 0; j < 9; ++j) a.v[j] = V + j * s.maxn;
@@ -272,7 +274,7 @@ gadi_status run_group(const Group &g, int threads, const gadi_sweep_instance *di
     const void *kern = pick_kernel(g.dim, g.r);
     const int nitems = (int)g.items.size();
     const int blocks = std::min(resident_blocks(kern, threads), nitems);
-    const size_t per_block = (256 + (size_t)g.maxn * (3 * sizeof(double) + sizeof(float) + 9 * sizeof(__half)) + 255) / 256 * 256;
+    const size_t per_block = (256 + (size_t)g.maxn * (4 * sizeof(double) + sizeof(float) + 9 * sizeof(__half)) + 255) / 256 * 256;
     DevBuf items, next, rec, scratch;
     SW_CK(cudaMalloc(&items.p, nitems * sizeof(SweepItem)));
     SW_CK(cudaMalloc(&next.p, sizeof(int)));
