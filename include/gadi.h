@@ -155,6 +155,17 @@ GADI_API gadi_status gadi_set_stop(gadi_solver *h, gadi_stop kind);
  * returns INVALID_ARG. */
 GADI_API gadi_status gadi_set_kernel(gadi_solver *h, gadi_kernel kind);
 
+/* FP16 inner scaling (default on = 1). on: the operator, the residual and
+ * the first correction are scaled by powers of two so that FP16 stays in
+ * range, alpha is added in FP32 and (2 - omega) alpha is folded into the
+ * FP64 update (Alg. 1 with the readings stated in the oracle). off = 0: the
+ * unscaled FP16 inner precision the paper's FP16 experiments show (Table
+ * "3d", the stall at 1e-8 to 1e-10): alpha is rounded into the stored FP16
+ * diagonals of aI + M and aI + N, r and z are not scaled, and (2 - omega)
+ * alpha multiplies z in FP16 before the second solve. An ablation mode; it
+ * only affects u_r = GADI_F16. Other values return INVALID_ARG. */
+GADI_API gadi_status gadi_set_scaling(gadi_solver *h, int32_t on);
+
 /* Rows per work item of the stencil kernels (an implementation choice, not
  * part of the paper's method: operator applications are bit-identical for
  * every value; the dot products of a solve sum in another order):

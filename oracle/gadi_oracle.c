@@ -736,8 +736,10 @@ int or_gadi_ir(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
  *   which 1: y = fl(H' x),  H' = 2^-sM (aI + M)
  *   which 2: y = fl(S' x),  S' = 2^-sN (aI + N)
  *   which 3: y = fl(S'^T x)
- * prec: OR_PREC_HALF, OR_PREC_SINGLE or OR_PREC_DOUBLE; x holds values of
- * that precision (as doubles). The scale exponents used are returned. */
+ * prec: OR_PREC_HALF, OR_PREC_HALF_NAIVE, OR_PREC_SINGLE or OR_PREC_DOUBLE;
+ * x holds values of that precision (as doubles). The scale exponents used
+ * are returned (zero in the naive mode, where alpha is rounded into the
+ * stored FP16 diagonal as in or_gadi_ir_split). */
 int or_lp_apply(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
                 const double *m_user, double alpha, int which, int prec,
                 const double *x, double *y, int32_t *sM_out, int32_t *sN_out)
@@ -752,9 +754,10 @@ int or_lp_apply(int64_t n, const int32_t *rp, const int32_t *ci, const double *a
     }
     int32_t *rpt, *cit; double *nvt;
     transpose_csr(n, rp, ci, nv, &rpt, &cit, &nvt);
-    const int half = prec == OR_PREC_HALF;
+    const int half = prec == OR_PREC_HALF || prec == OR_PREC_HALF_NAIVE;
+    const int naive = prec == OR_PREC_HALF_NAIVE;
     int sM = 0, sN = 0;
-    if (half) {
+    if (half && !naive) {
         sM = half_scale_exponent(n, rp, m, alpha);
         sN = half_scale_exponent(n, rp, nv, alpha);
         int sNt = half_scale_exponent(n, rpt, nvt, alpha);
@@ -773,11 +776,16 @@ int or_lp_apply(int64_t n, const int32_t *rp, const int32_t *ci, const double *a
         size_t szvf = (size_t)(n > 0 ? n : 1) * sizeof(float);
         float *vf = (float *)malloc(szmf), *xf = (float *)malloc(szvf), *yf = (float *)malloc(szvf);
         const double *src = which == 1 ? m : (which == 2 ? nv : nvt);
+        const int32_t *rpx = which == 3 ? rpt : rp, *cix = which == 3 ? cit : ci;
         int s = which == 1 ? sM : sN;
-        for (int64_t k = 0; k < nnz; ++k)
-            vf[k] = half ? (float)(_Float16)ldexp(src[k], -s) : (float)src[k];
+        for (int64_t i = 0; i < n; ++i)
+            for (int32_t k = rpx[i]; k < rpx[i + 1]; ++k) {
+                /* naive: alpha rounded into the stored diagonal, nothing scaled */
+                double v = naive ? src[k] + (cix[k] == i ? alpha : 0.0) : ldexp(src[k], -s);
+                vf[k] = half ? (float)(_Float16)v : (float)src[k];
+            }
         for (int64_t i = 0; i < n; ++i) xf[i] = (float)x[i];
-        float sig = (float)ldexp(alpha, -s);
+        float sig = naive ? 0.0f : (float)ldexp(alpha, -s);
         if (which == 3) spmv32(n, rpt, cit, vf, sig, xf, yf, half);
         else spmv32(n, rp, ci, vf, sig, xf, yf, half);
         for (int64_t i = 0; i < n; ++i) y[i] = (double)yf[i];

@@ -141,6 +141,27 @@ __global__ void k_demote(int64_t cnt, const double *src, __half *dst, double sca
         dst[i] = __double2half(__dmul_rn(src[i], scale));
 }
 
+// unscaled FP16 mode: dst = fl16(sign src + alpha) on the stored diagonal
+// (the first slot of a row whose column is the row; padding slots come after
+// the row's entries), fl16(sign src) elsewhere. W = 0: every entry is a
+// diagonal. sign = -1 forms N^T = -N of a skew-symmetric N.
+__global__ void k_demote_diag(int64_t cnt, int W, const int *col, const double *src, __half *dst,
+                              double alpha, double sign)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool diag = W == 0;
+        if (!diag) {
+            const int64_t row = i / W, k0 = row * W;
+            diag = col[i] == row;
+            for (int64_t k = k0; k < i && diag; ++k)
+                if (col[k] == row) diag = false;
+        }
+        const double v = sign < 0.0 ? -src[i] : src[i];
+        dst[i] = __double2half(diag ? __dadd_rn(v, alpha) : v);
+    }
+}
+
 __global__ void k_count_range(int64_t cnt, const double *src, const __half *dst, int *lost)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
@@ -275,6 +296,8 @@ struct gadi_solver {
     int sM = 0, sNs = 0;
     bool demoted = false;
     double demoted_alpha = 0.0;
+    int scaling = 1;          // 0: unscaled FP16 inner mode (alpha rounded into the FP16 diagonal)
+    int demoted_scaling = 1;
     // work
     double *bdev = nullptr, *xdev = nullptr, *r64 = nullptr;
     double *x2 = nullptr;     // second iterate buffer (the iterates alternate with x)
@@ -382,18 +405,47 @@ gadi_status prepare_inner(gadi_solver *h)
         h->sM = h->sNs = 0;
         return GADI_OK;
     }
-    int sM = half_scale_exponent(h->mnorm, h->alpha);
-    int sN = half_scale_exponent(h->nnorm, h->alpha);
-    if (h->demoted && sM == h->sM && sN == h->sNs) return GADI_OK;
+    const bool naive = h->scaling == 0;
+    int sM = naive ? 0 : half_scale_exponent(h->mnorm, h->alpha);
+    int sN = naive ? 0 : half_scale_exponent(h->nnorm, h->alpha);
+    if (h->demoted && sM == h->sM && sN == h->sNs && h->demoted_scaling == h->scaling &&
+        (!naive || h->demoted_alpha == h->alpha))
+        return GADI_OK;
     const int64_t cnt = h->n * (int64_t)h->W;
     const double scM = std::ldexp(1.0, -sM), scN = std::ldexp(1.0, -sN);
-    k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->em, h->m16, scM);
-    k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->en, h->n16, scN);
-    if (h->ent) k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->ent, h->nt16, scN);
-    if (h->HD64) {
-        k_demote<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HD64, h->HD16, scM);
-        for (int d = 0; d < h->sdim; ++d)
-            k_demote<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HK64[d], h->HK16[d], scM);
+    if (naive) {
+        // alpha rounded into the stored FP16 diagonals of H and S, nothing scaled
+        // S^T = aI + N^T keeps +alpha on its diagonal, so N^T gets its own
+        // FP16 array here even when N is skew-symmetric
+        if (!h->nt16 && dalloc(&h->nt16, cnt) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, GADI_ERR_OUT_OF_MEMORY, "no memory for the unscaled S^T values");
+        }
+        k_demote_diag<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->em, h->m16,
+                                                                      h->alpha, 1.0);
+        k_demote_diag<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->en, h->n16,
+                                                                      h->alpha, 1.0);
+        if (h->ent)
+            k_demote_diag<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->ent, h->nt16,
+                                                                          h->alpha, 1.0);
+        else
+            k_demote_diag<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->en, h->nt16,
+                                                                          h->alpha, -1.0);
+        if (h->HD64) {
+            k_demote_diag<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, 0, nullptr, h->HD64, h->HD16,
+                                                                           h->alpha, 1.0);
+            for (int d = 0; d < h->sdim; ++d)
+                k_demote<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HK64[d], h->HK16[d], 1.0);
+        }
+    } else {
+        k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->em, h->m16, scM);
+        k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->en, h->n16, scN);
+        if (h->ent) k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->ent, h->nt16, scN);
+        if (h->HD64) {
+            k_demote<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HD64, h->HD16, scM);
+            for (int d = 0; d < h->sdim; ++d)
+                k_demote<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HK64[d], h->HK16[d], scM);
+        }
     }
     CK(cudaGetLastError());
     // entries that flush to zero or overflow in FP16 even after scaling
@@ -409,6 +461,8 @@ gadi_status prepare_inner(gadi_solver *h)
     h->sM = sM;
     h->sNs = sN;
     h->demoted = true;
+    h->demoted_alpha = h->alpha;
+    h->demoted_scaling = h->scaling;
     return GADI_OK;
 }
 
@@ -424,14 +478,15 @@ EllOp<T> make_ell(const gadi_solver *h)
     if constexpr (std::is_same<T, __half>::value) {
         op.m = h->m16;
         op.nv = h->n16;
-        op.nt = h->ent ? h->nt16 : nullptr;
+        op.nt = (h->ent || h->scaling == 0) ? h->nt16 : nullptr;
     } else {
         op.m = h->em;
         op.nv = h->en;
         op.nt = h->ent;
     }
-    op.sigH = (Acc)std::ldexp(h->alpha, -h->sM);
-    op.sigS = (Acc)std::ldexp(h->alpha, -h->sNs);
+    const bool naive = h->scaling == 0 && std::is_same<T, __half>::value;
+    op.sigH = naive ? Acc(0) : (Acc)std::ldexp(h->alpha, -h->sM);
+    op.sigS = naive ? Acc(0) : (Acc)std::ldexp(h->alpha, -h->sNs);
     return op;
 }
 
@@ -457,7 +512,20 @@ StencilOp<T, DIM, R> make_stencil(const gadi_solver *h)
         op.AU[d] = h->AU[d];
     }
     const double scM = std::ldexp(1.0, -h->sM), scN = std::ldexp(1.0, -h->sNs);
+    op.s_diag = Acc(0);
     if constexpr (std::is_same<T, __half>::value) {
+        if (h->scaling == 0) {
+            // unscaled: alpha rounded into the FP16 diagonals, added in the row's order
+            op.h_diag = half_round(h->a_diag + h->alpha);
+            op.h_off = half_round(h->m_off);
+            op.s_c = half_round(h->n_up);
+            op.s_diag = half_round(h->alpha);
+            op.HD = h->HD16;
+            for (int d = 0; d < 3; ++d) op.HK[d] = h->HK16[d];
+            op.sigH = Acc(0);
+            op.sigS = Acc(0);
+            return op;
+        }
         op.h_diag = half_round(h->a_diag * scM);
         op.h_off = half_round(h->m_off * scM);
         op.s_c = half_round(h->n_up * scN);
@@ -538,6 +606,7 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     a.sM = h->sM;
     a.sN = h->sNs;
     a.half = h->u_r == GADI_F16 ? 1 : 0;
+    a.naive = (h->u_r == GADI_F16 && h->scaling == 0) ? 1 : 0;
     a.stop_kind = h->stop;
     a.max_inner = h->max_inner;
     a.max_outer = h->max_outer;
@@ -889,6 +958,14 @@ gadi_status gadi_set_kernel(gadi_solver *h, gadi_kernel kind)
     if (kind == GADI_KERNEL_STENCIL && !h->has_stencil)
         return fail(h, GADI_ERR_INVALID_ARG, "the stencil kernels need a stencil descriptor at create");
     h->kernel = kind;
+    return GADI_OK;
+}
+
+gadi_status gadi_set_scaling(gadi_solver *h, int32_t on)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (on != 0 && on != 1) return fail(h, GADI_ERR_INVALID_ARG, "scaling must be 0 or 1");
+    h->scaling = on;
     return GADI_OK;
 }
 

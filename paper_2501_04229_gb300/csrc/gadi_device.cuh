@@ -226,7 +226,10 @@ __device__ __forceinline__ void block_reduce_w0(double (&v)[NS], const int (&ops
 // exchange (a block that sees ctl->error stops waiting at once). One block
 // needs no global memory at all.
 // ---------------------------------------------------------------------------
-struct GridExchange {
+// CH: blocks whose partials one lane loads per batch (32 CH blocks per
+// batch); kernels with a 64-register budget use fewer
+template <int CH>
+struct GridExchangeT {
     Ctl *ctl;
     double *part;                  // [2][kMaxSlots][gridDim]
     unsigned epoch;
@@ -281,7 +284,6 @@ struct GridExchange {
 #pragma unroll
             for (int s = 0; s < NS; ++s) acc[s] = V(0);
             if (ok) {
-                constexpr int CH = 4;
                 for (unsigned b0 = lane; b0 < G; b0 += 32 * CH) {
                     double w[CH][NS];
 #pragma unroll
@@ -321,5 +323,7 @@ struct GridExchange {
         return allreduce(v, ops);
     }
 };
+
+using GridExchange = GridExchangeT<4>;
 
 }  // namespace gadi

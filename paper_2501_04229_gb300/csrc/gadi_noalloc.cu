@@ -191,6 +191,7 @@ gadi_status launch(int dev, int num_sms, cudaStream_t stream, unsigned char *bas
     a.sM = sM;
     a.sN = sN;
     a.half = 1;
+    a.naive = 0;
     a.stop_kind = GADI_STOP_ETA;
     a.max_inner = max_inner;
     a.max_outer = max_outer;

@@ -207,7 +207,7 @@ struct XAxpy2 {                      // fl(a - c fl(b + d e))  (C-G residual upd
 };
 
 template <class T>
-struct XScale {                      // fl(c a), c a power of two
+struct XScale {                      // fl(c a): c a power of two, or (2-w) a in the unscaled mode
     using Acc = typename Prec<T>::Acc;
     using P = Prec<T>;
     const T *a;
@@ -350,6 +350,9 @@ struct StencilOp {
     const T *__restrict__ HD;
     const T *__restrict__ HK[3];
     Acc sigH, sigS;
+    // unscaled FP16 mode: alpha rounded to T as S's stored diagonal, added at
+    // the diagonal's place in the row (zero otherwise: alpha is in sigS)
+    Acc s_diag;
 
     // grid coordinates of node i (x fastest); n < 2^31 is enforced at create
     __device__ __forceinline__ void coords(int64_t i, unsigned (&cd)[3]) const
@@ -417,6 +420,7 @@ struct StencilOp {
 #pragma unroll
         for (int d = DIM - 1; d >= 0; --d)
             if (cd[d] > 0) acc = P::madd(acc, lo, f.one(i - stride(d)));
+        if (s_diag != Acc(0)) acc = P::madd(acc, s_diag, fi);
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
             if (cd[d] < last) acc = P::madd(acc, -lo, f.one(i + stride(d)));
@@ -558,6 +562,9 @@ struct StencilOp {
                     for (int k = 0; k < R; ++k)
                         if (k > 0 || cd[0] > 0) acc[k] = P::madd(acc[k], lo, k ? c[k - 1] : xm);
                 }
+                if (s_diag != Acc(0))
+#pragma unroll
+                    for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], s_diag, c[k]);
                 {
                     const Acc xp = cd[0] + R <= last ? f.one(i0 + R) : Acc(0);
 #pragma unroll

@@ -42,6 +42,7 @@ struct SolveArgs {
     T *v[9];                     // inner work vectors, n elements each
     double anorm, bnorm, tol, eps, pfac;
     int sM, sN, half, stop_kind;
+    int naive;                   // unscaled FP16 mode: no 2^-e, 2^-ez; (2-w) a applied to z in FP16
     int max_inner, max_outer;
     Ctl *ctl;
     double *part;                // [2][kMaxSlots][gridDim] partial sums
@@ -57,13 +58,13 @@ constexpr int kRacedOut = 100;
 // launch bound: 1024 threads for one-row items, 512 for 4- and 8-row items
 // (whose per-thread state is larger)
 template <class Op>
-constexpr int max_threads() { return Op::R > 1 ? 512 : 1024; }
+__host__ __device__ constexpr int max_threads() { return Op::R > 1 ? 512 : 1024; }
 
 // The solve, run by a team of threads: the whole grid (ex.block_only false,
 // t0/nt the global thread index and count) or one block (ex.block_only true,
 // t0/nt the block's). lead is the one thread that writes the results.
-template <class Op, class T>
-__device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchange &ex, const int64_t t0,
+template <class Op, class T, class Ex>
+__device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, const int64_t t0,
                                            const int64_t nt, const bool lead)
 {
     using P = Prec<T>;
@@ -152,7 +153,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
         }
 
         // ---- D: r^ = fl_r(2^-e r), u = H' r^, z = 0 (CG start) ----------------
-        const int e = (a.half && rinf > 0.0) ? ilogb(rinf) : 0;
+        const int e = (a.half && !a.naive && rinf > 0.0) ? ilogb(rinf) : 0;
         T *rc = a.v[0], *rn = a.v[1], *uc = a.v[2], *un = a.v[3];
         T *sc = a.v[4], *sn = a.v[5], *p = a.v[6];
         Acc g[2] = {0, 0};
@@ -271,11 +272,12 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
         itH += it_cg;
 
         // ---- C0: ez, z^ = 2^-ez z, s = S'^T z^, p = s, y = 0 (CGNR start) -------
-        const int ez = (a.half && zinf > Acc(0) && isfinite((double)zinf)) ? ilogb((double)zinf) : 0;
+        const int ez = (a.half && !a.naive && zinf > Acc(0) && isfinite((double)zinf)) ? ilogb((double)zinf) : 0;
         T *rsc = a.v[0], *rsn = a.v[1], *s = a.v[2], *pc = a.v[3], *pn = a.v[4], *q = a.v[5], *y = a.v[6];
         Acc c0[2] = {0, 0};
         {
-            const XScale<T> fz{z, (Acc)ldexp(1.0, -ez)};
+            // z^ = 2^-ez z; unscaled mode: (2-w) a z formed in the inner precision
+            const XScale<T> fz{z, a.naive ? (Acc)a.pfac : (Acc)ldexp(1.0, -ez)};
             Acc l0 = 0, l1 = 0;
             for (int64_t it = t0; it < items; it += nt) {
                 Acc rs[R], ss[R], yy[R];
@@ -305,7 +307,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
         //   x_next = x + (2-w) a 2^(e - sM + ez - sN) y
         // for its own rows; after the last pass x_next is the new iterate, so
         // no separate update pass and grid synchronisation are needed.
-        const double upd = ldexp(a.pfac, e - a.sM + ez - a.sN);
+        const double upd = a.naive ? 1.0 : ldexp(a.pfac, e - a.sM + ez - a.sN);
         double *const xnext = xcur == a.x ? a.x2 : a.x;
         int it_s = 0;
         if (rr0s > Acc(0)) {
@@ -424,7 +426,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, GridExchan
 template <class Op, class T>
 __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const SolveArgs<Op, T> a)
 {
-    GridExchange ex{a.ctl, a.part, 0u, a.wait_ns, a.extra, false};
+    // one batch of partial loads covers 160 blocks (152 SMs) where registers allow
+    GridExchangeT<(max_threads<Op>() >= 1024 ? 4 : 5)> ex{a.ctl, a.part, 0u, a.wait_ns, a.extra, false};
     solve_body(a, ex, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
                blockIdx.x == 0 && threadIdx.x == 0);
 }

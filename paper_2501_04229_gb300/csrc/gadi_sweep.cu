@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(512, 1) gadi_sweep_kernel(const SweepArgs s)
         a.sM = sM;
         a.sN = sN;
         a.half = 1;
+        a.naive = 0;
         a.stop_kind = 0;
         a.max_inner = s.max_inner;
         a.max_outer = s.max_outer;

@@ -26,7 +26,7 @@ OP_A, OP_H, OP_S, OP_ST = 0, 1, 2, 3
 
 # every entry point declared in include/gadi.h
 EXPORTS = [
-    "gadi_create", "gadi_set_params", "gadi_set_inner", "gadi_set_stop", "gadi_set_kernel", "gadi_set_item_rows",
+    "gadi_create", "gadi_set_params", "gadi_set_inner", "gadi_set_stop", "gadi_set_kernel", "gadi_set_item_rows", "gadi_set_scaling",
     "gadi_set_launch", "gadi_set_wait_limit", "gadi_debug_force_timeout", "gadi_solve",
     "gadi_apply", "gadi_get_scales", "gadi_predict_params", "gadi_destroy", "gadi_status_str",
     "gadi_last_error", "gadi_solve_stencil_noalloc", "gadi_sweep", "gadi_model_fit",
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         "gadi_set_stop": (i32, [vp, i32]),
         "gadi_set_kernel": (i32, [vp, i32]),
         "gadi_set_item_rows": (i32, [vp, i32]),
+        "gadi_set_scaling": (i32, [vp, i32]),
         "gadi_set_launch": (i32, [vp, i32, i32]),
         "gadi_set_wait_limit": (i32, [vp, f64]),
         "gadi_debug_force_timeout": (i32, [vp, i32]),
@@ -210,6 +211,10 @@ def gadi_set_kernel(h, kind):
 
 def gadi_set_item_rows(h, rows):
     _check(h, load().gadi_set_item_rows(h, int(rows)))
+
+
+def gadi_set_scaling(h, on):
+    _check(h, load().gadi_set_scaling(h, int(on)))
 
 
 def gadi_set_launch(h, grid_blocks=0, block_threads=0):

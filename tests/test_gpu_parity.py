@@ -484,3 +484,97 @@ def test_empty_system_rejected():
     with pytest.raises(G.GadiError) as e:
         G.gadi_create(np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
     assert e.value.status == G.GADI_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------------------
+# unscaled ("naive") FP16 inner precision: the ablation of §4.1's FP16 runs
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["2d_33_b10", "3d_13_b100", "3d_12_b50_grf"])
+@pytest.mark.parametrize("kernel", [G.GADI_KERNEL_SPARSE, G.GADI_KERNEL_STENCIL])
+@pytest.mark.parametrize("alpha", [0.01, 3.0])
+def test_naive_apply_bit_exact(name, kernel, alpha):
+    p = PROBLEMS[name]()
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, alpha, 1.0, u_r=G.GADI_F16)
+        G.gadi_set_scaling(h, 0)
+        G.gadi_set_kernel(h, kernel)
+        for which in (G.OP_H, G.OP_S, G.OP_ST):
+            x = _half_vector(p.n, 50 + which)
+            want, sM, sN = oracle.lp_apply(p.A, alpha, which, oracle.PREC_HALF_NAIVE, x)
+            xd = _dev(x, torch.float16)
+            yd = torch.empty_like(xd)
+            G.gadi_apply(h, which, xd, yd)
+            torch.cuda.synchronize()
+            got = yd.double().cpu().numpy()
+            assert np.array_equal(got, want), (which, np.abs(got - want).max())
+        assert G.gadi_get_scales(h) == (0, 0) == (sM, sN)
+    finally:
+        G.gadi_destroy(h)
+
+
+def test_naive_apply_item_rows_bit_exact():
+    p = ROWS_PROBLEMS["3d_16_b40"]()
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 0.37, 1.0, u_r=G.GADI_F16)
+        G.gadi_set_scaling(h, 0)
+        G.gadi_set_kernel(h, G.GADI_KERNEL_STENCIL)
+        for rows in (1, 4, 8):
+            G.gadi_set_item_rows(h, rows)
+            for which in (G.OP_H, G.OP_S, G.OP_ST):
+                x = _half_vector(p.n, 60 + which)
+                want, _, _ = oracle.lp_apply(p.A, 0.37, which, oracle.PREC_HALF_NAIVE, x)
+                xd = _dev(x, torch.float16)
+                yd = torch.empty_like(xd)
+                G.gadi_apply(h, which, xd, yd)
+                torch.cuda.synchronize()
+                assert np.array_equal(yd.double().cpu().numpy(), want), (rows, which)
+    finally:
+        G.gadi_destroy(h)
+
+
+@pytest.mark.parametrize("kernel", [G.GADI_KERNEL_SPARSE, G.GADI_KERNEL_STENCIL])
+def test_naive_fp16_stalls_like_the_oracle(kernel):
+    """Table '3d' (§4.1): without scaling the FP16-inner iteration stalls (or
+    breaks down) far above double accuracy, on the GPU as in the oracle;
+    scaled it reaches RES 1e-13."""
+    p = P.make_problem(3, 8, 1.0, rhs="ones")
+    _, onaive, _ = oracle.gadi_ir(p.A, p.b, 0.5, 1.0, tol=1e-13, stop=oracle.STOP_RES, eps_inner=1e-2,
+                                  max_outer=400, max_inner=300, prec=oracle.PREC_HALF_NAIVE)
+    assert onaive["status"] != oracle.OK and onaive["res_rel"] > 1e-9
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 0.5, 1.0, u_r=G.GADI_F16)
+        G.gadi_set_inner(h, 1e-2, 300, 400)
+        G.gadi_set_stop(h, G.GADI_STOP_RES)
+        G.gadi_set_kernel(h, kernel)
+        G.gadi_set_scaling(h, 0)
+        st, info, _ = _solve(h, p, 1e-13)
+        assert st != G.GADI_OK and info["res_rel"] > 1e-9
+        G.gadi_set_scaling(h, 1)
+        st, info, _ = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK and info["res_rel"] <= 1e-13
+    finally:
+        G.gadi_destroy(h)
+
+
+def test_naive_fp16_loose_tolerance_matches_oracle():
+    p = PROBLEMS["3d_13_b100"]()
+    want, oinfo, _ = oracle.gadi_ir(p.A, p.b, 3.0, 1.0, tol=1e-6, eps_inner=1e-2, prec=oracle.PREC_HALF_NAIVE,
+                                    max_outer=3000)
+    assert oinfo["status"] == oracle.OK
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 3.0, 1.0, u_r=G.GADI_F16)
+        G.gadi_set_inner(h, 1e-2, 200, 3000)
+        G.gadi_set_scaling(h, 0)
+        st, info, x = _solve(h, p, 1e-6)
+        assert st == G.GADI_OK, G.last_error(h)
+        assert oracle.backward_error(p.A, p.b, x) <= 1e-6
+        assert abs(info["outer_iters"] - oinfo["outer_iters"]) <= max(2, 0.15 * oinfo["outer_iters"])
+        with pytest.raises(G.GadiError):
+            G.gadi_set_scaling(h, 2)
+    finally:
+        G.gadi_destroy(h)

@@ -251,6 +251,28 @@ def test_naive_fp16_stalls_scaled_fp16_does_not(oracle_lib):
         assert bad["status"] != oracle_lib.OK and bad["res_rel"] > 1e-9
 
 
+@pytest.mark.parametrize("alpha,shift_m,shift_n", [(0.5, 0.5, 0.5), (0.01, 0.01171875, 0.01000213623046875)])
+def test_naive_apply_is_exact_product_with_rounded_diagonal(oracle_lib, alpha, shift_m, shift_n):
+    """Unscaled FP16 operators (alpha rounded into the stored FP16 diagonal,
+    §4.1's FP16 runs): with beta h / 2 = 1/4 and 2D diagonal 4, every stored
+    value is exact in FP16 except the shifted diagonals: fl16(4 + alpha) = 4 +
+    shift_m (FP16 spacing 2^-8 at 4: 0.01 becomes 3 * 2^-8) and fl16(0 +
+    alpha) = shift_n. With small integer x the FP32 row sums are exact, so the
+    applications equal the exact products (shift_m I + M)x, (shift_n I + N)x
+    and (shift_n I + N)^T x, rounded once to FP16 where they are stored."""
+    p = P.make_problem(2, 7, 4.0, rhs="ones")            # h = 1/8, beta h / 2 = 1/4
+    rng = np.random.default_rng(3)
+    x = rng.integers(-8, 9, p.n).astype(np.float64)
+    A = p.A.to_dense()
+    Md, Nd = (A + A.T) / 2, (A - A.T) / 2
+    I = np.eye(p.n)
+    assert float(np.float16(4 + alpha)) - 4 == shift_m and float(np.float16(alpha)) == shift_n
+    for which, K in ((1, Md + shift_m * I), (2, Nd + shift_n * I), (3, (Nd + shift_n * I).T)):
+        y, sM, sN = oracle_lib.lp_apply(p.A, alpha, which, oracle_lib.PREC_HALF_NAIVE, x)
+        assert (sM, sN) == (0, 0)
+        assert np.array_equal(y, (K @ x).astype(np.float16).astype(np.float64)), which
+
+
 def test_outer_steps_u_shaped_in_alpha(oracle_lib):
     """Table 'alpha-effects' (§4.1): small and large alpha both need many more
     outer steps than a moderate alpha."""
