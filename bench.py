@@ -11,8 +11,12 @@ when a step's timing starts; L2 (129 MB) is flushed before every timed
 step by writing a 256 MB buffer (outside the timed region).
 
 Prints one JSON line. Secondary numbers in the line: the same solve with
-plain FP64 GADI (inner eps 1e-10) on the same GPU, and operator-application
-bandwidths per kernel variant.
+plain FP64 GADI (inner eps 1e-10) on the same GPU, operator-application
+bandwidths per kernel variant, and the HBM-bound case: the same method on
+the 192^3 system (working set several times L2) with its effective
+bandwidth against the measured HBM peak and FP64 GADI beside it.
+--workload selects another system of problems.WORKLOADS for the main
+measurement (used for profiling runs; the default is the metric's).
 
 Under torchrun (N > 1) every rank solves its own copy of the system
 (replicas: a single solve is not sharded), the step time is the maximum
@@ -40,6 +44,7 @@ TOL = 1e-13
 ALPHA, OMEGA = 3.0, 0.0          # best of an (alpha, omega, eps) sweep on this workload
 EPS16 = 1e-1
 EPS64 = 1e-10
+HBM_ALPHA, HBM_OMEGA = 2.0, 0.0  # best of alpha in {2, 3, 4.5} on the 192^3 system
 
 
 def parse():
@@ -56,6 +61,8 @@ def parse():
                          "3D systems (untimed set-up), or the fixed --alpha/--omega")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GADI comparison")
     ap.add_argument("--no-spmv", action="store_true", help="skip the operator bandwidth runs")
+    ap.add_argument("--no-hbm", action="store_true", help="skip the 192^3 HBM-bound case")
+    ap.add_argument("--workload", default=WORKLOAD, help="system of problems.WORKLOADS to time")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0,
                     help="bound on the CPU oracle's time for cpu_baseline")
     return ap.parse_args()
@@ -220,11 +227,11 @@ def apply_bandwidth(G, torch, p, stencil, kernels, flush_l2, stream, reps=10):
     return out
 
 
-def learned_params(G, workload_n, workload_beta):
+def learned_params(G, queries):
     """Training records from a batched sweep of small 3D systems of the same
     structure (sides 8..48, 5 convection strengths, 12 alpha x 3 omega), then
-    the MLP (trained on the GPU) and the GPR; their (alpha, omega) for the
-    workload's (log n, log beta)."""
+    the MLP (trained on the GPU) and the GPR; their (alpha, omega) for each
+    (n, beta) of queries (the first one is reported at the top level)."""
     from paper_2501_04229_gb300 import sweep as SW
     inst = [(3, N, b) for N in (8, 16, 24, 32, 40, 48) for b in (2.0, 10.0, 40.0, 100.0, 300.0)]
     cands = SW.candidates(n_alpha=12, omegas=(0.0, 0.5, 1.0), lo=-1.0, hi=1.5)
@@ -234,7 +241,7 @@ def learned_params(G, workload_n, workload_beta):
     rows = [r for r in recs if r["best"]]
     X = np.array([[r["log_n"], r["log_beta"]] for r in rows])
     Y = np.array([[math.log(r["best"]["alpha"]), r["best"]["omega"]] for r in rows])
-    q = np.array([[math.log(workload_n), math.log(workload_beta)]])
+    q = np.array([[math.log(qn), math.log(qb)] for qn, qb in queries])
     out = {"train_instances": len(rows), "candidates": len(cands), "sweep_s": round(t_sweep, 3)}
     t0 = time.perf_counter()
     mlp = G.gadi_model_fit(G.GADI_MODEL_MLP, X, Y, hyper=[3000, 1e-2, 1])
@@ -242,11 +249,89 @@ def learned_params(G, workload_n, workload_beta):
     gpr = G.gadi_model_fit(G.GADI_MODEL_GPR, X, Y)
     try:
         for name, m in (("mlp", mlp), ("gpr", gpr)):
-            y = G.gadi_model_predict(m, q)[0]
-            out[name] = {"alpha": float(math.exp(y[0])), "omega": float(min(1.999, max(0.0, y[1])))}
+            ys = G.gadi_model_predict(m, q)
+            preds = [{"alpha": float(math.exp(y[0])), "omega": float(min(1.999, max(0.0, y[1])))} for y in ys]
+            out[name] = preds[0]
+            out[name + "_all"] = preds
     finally:
         G.gadi_model_destroy(mlp)
         G.gadi_model_destroy(gpr)
+    return out
+
+
+def hbm_case(G, torch, P, predictor, args, flush_l2, stream, N, beta):
+    """FP16-inner GADI-IR on the 192^3 system, whose vectors (14 MB each in
+    FP16, 57 MB in FP64) stream from HBM: two timed solves after one warm-up
+    (L2 flushed before each), the effective bandwidth of the solve kernel
+    (algorithmic bytes over its mean time) against the measured HBM peak,
+    and one plain FP64 GADI solve on the same GPU."""
+    p = P.workload(f"convdiff3d_{N}_b{beta:g}")
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
+    h = G.gadi_create(t(p.A.row_ptr, torch.int32), t(p.A.col_idx, torch.int32), t(p.A.val),
+                      stencil=(3, N, beta, 0), stream=stream.cuda_stream)
+    b = t(p.b)
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    src = "fixed"
+    alpha, omega = HBM_ALPHA, HBM_OMEGA
+    if predictor is not None and args.params != "fixed":
+        src = args.params
+        alpha, omega = predictor[args.params + "_all"][1]["alpha"], predictor[args.params + "_all"][1]["omega"]
+    out = {"workload": f"convdiff3d_{N}_b{beta:g}", "n": p.n}
+    try:
+        G.gadi_set_kernel(h, G.GADI_KERNEL_STENCIL)
+
+        def solve(a, w, u_r, eps, max_inner):
+            G.gadi_set_params(h, a, w, u_r=u_r)
+            G.gadi_set_inner(h, eps, max_inner, 100000)
+            x.zero_()
+            flush_l2()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, info = G.gadi_solve(h, b, x, TOL)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return st, info, e0.elapsed_time(e1) * 1e-3
+
+        st, info, _ = solve(alpha, omega, G.GADI_F16, EPS16, 500)
+        if st != G.GADI_OK:
+            out["fallback"] = {"from": {"source": src, "alpha": alpha, "omega": omega}, "status": G.status_str(st)}
+            src, alpha, omega = "fixed", HBM_ALPHA, HBM_OMEGA
+        times, kt = [], []
+        for _ in range(2):
+            st, info, dt = solve(alpha, omega, G.GADI_F16, EPS16, 500)
+            assert st == G.GADI_OK, G.last_error(h)
+            times.append(dt)
+            kt.append(info["t_solve_s"])
+        eta = info["eta_inf"]
+        fwd = float((x.cpu() - torch.from_numpy(p.x_exact)).abs().max())
+        achieved = algorithmic_bytes(p.n, p.A.nnz, info, "stencil", True) / statistics.mean(kt) / 1e9
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except OSError:
+            pass
+        peak = peaks.get("hbm_gbs", 6800.0)
+        out.update({
+            "time_s": statistics.mean(times), "params": {"source": src, "alpha": alpha, "omega": omega},
+            "eta_inf": eta, "max_abs_err_vs_exact": fwd,
+            "solve": {k: info[k] for k in ("outer_iters", "inner_iters_H", "inner_iters_S", "spmv_count",
+                                           "grid_blocks", "block_threads")},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4),
+                         "traffic": profiled_traffic(f"gadi_solve_kernel_convdiff3d_{N}_b{beta:g}.md"),
+                         "kernel": "gadi_solve_kernel<StencilOp<half,3,8>>",
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
+        })
+        if not args.no_fp64:
+            st64, i64, t64 = solve(HBM_ALPHA, HBM_OMEGA, G.GADI_F64, EPS64, 10000)
+            out["fp64_gadi_same_gpu"] = {"time_s": t64, "status": G.status_str(st64), "alpha": HBM_ALPHA,
+                                         "omega": HBM_OMEGA, "outer_iters": i64["outer_iters"],
+                                         "eta_inf": i64["eta_inf"]}
+            if st64 == G.GADI_OK:
+                out["speedup_vs_fp64_gadi"] = t64 / out["time_s"]
+    finally:
+        G.gadi_destroy(h)
     return out
 
 
@@ -259,12 +344,13 @@ def run_gpu(args, rank, world):
     B.build()
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    p = P.workload(WORKLOAD)
+    p = P.workload(args.workload)
     n, nnz = p.n, p.A.nnz
     stream = torch.cuda.current_stream()
     t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
+    stencil = (p.dim, p.N, p.beta, 1 if p.faces is not None else 0)
     h = G.gadi_create(t(p.A.row_ptr, torch.int32), t(p.A.col_idx, torch.int32), t(p.A.val),
-                      stencil=(3, p.N, p.beta, 0), stream=stream.cuda_stream)
+                      stencil=stencil, stream=stream.cuda_stream)
     kern = G.GADI_KERNEL_STENCIL if args.kernel == "stencil" else G.GADI_KERNEL_SPARSE
     G.gadi_set_kernel(h, kern)
     b = t(p.b)
@@ -277,9 +363,10 @@ def run_gpu(args, rank, world):
         flush.fill_(1.0)
         flush.sum()
 
+    HBM_N, HBM_BETA = 192, 100.0
     predictor = None
     if args.params != "fixed":
-        predictor = learned_params(G, n, p.beta)
+        predictor = learned_params(G, [(n, p.beta), (HBM_N ** 3, HBM_BETA)])
         args.alpha = predictor[args.params]["alpha"]
         args.omega = predictor[args.params]["omega"]
 
@@ -355,6 +442,11 @@ def run_gpu(args, rank, world):
     G.gadi_set_kernel(h, kern)
     configure(G.GADI_F16)
 
+    # the HBM-bound case: the same method on the 192^3 system
+    hbm_res = None
+    if not args.no_hbm and args.workload == WORKLOAD:
+        hbm_res = hbm_case(G, torch, P, predictor, args, flush_l2, stream, HBM_N, HBM_BETA)
+
     # end to end through the C ABI with pinned host buffers (copies inside)
     bh = torch.from_numpy(p.b.copy()).pin_memory()
     xh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -380,20 +472,20 @@ def run_gpu(args, rank, world):
     achieved = algorithmic_bytes(n, nnz, info, args.kernel, True) / statistics.mean(kern_t) / 1e9
     return {
         "ms_per_step": ms_per_step, "value": tot / args.steps, "info": info, "eta_gpu": eta_gpu,
-        "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(),
+        "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(), "hbm_case": hbm_res,
         "e2e": statistics.mean(e2e), "predictor": predictor, "roofline": {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4),
-            "traffic": profiled_traffic("gadi_solve_kernel_convdiff3d_64_b100.md") if args.kernel == "stencil" else None,
+            "traffic": profiled_traffic(f"gadi_solve_kernel_{args.workload}.md") if args.kernel == "stencil" else None,
             "kernel": "gadi_solve_kernel<StencilOp<half,3,8>>" if args.kernel == "stencil"
             else "gadi_solve_kernel<EllOp<half>>",
-            "note": "whole solve in one persistent launch; the 64^3 working set is L2-resident, so this is an effective rate",
+            "note": "whole solve in one persistent launch; at 64^3 the working set is L2-resident, so this is an effective rate (the HBM-bound case is hbm_case)",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
         "kernel_time_s": statistics.mean(kern_t),
     }
 
 
-def cpu_oracle_time(p, alpha, omega, budget_s):
+def cpu_oracle_time(p, alpha, omega, budget_s, name=WORKLOAD):
     """The oracle (FP64-inner GADI-IR, all host cores) on the same system,
     bounded: a full solve when it fits the budget, else max_outer steps
     scaled to the outer-step count of a full solve."""
@@ -413,11 +505,11 @@ def cpu_oracle_time(p, alpha, omega, budget_s):
     dt = time.perf_counter() - t0
     if info["status"] == oracle.OK:
         return {"value": dt, "unit": "s", "cores": cores, "kind": "oracle",
-                "sample": f"one full FP64-inner GADI-IR solve of {WORKLOAD} to eta 1e-13 "
+                "sample": f"one full FP64-inner GADI-IR solve of {name} to eta 1e-13 "
                           f"({info['outer_iters']} outer steps)"}, x, info
     # not finished within the budget: extrapolate per outer step
     return {"value": None, "unit": "s", "cores": cores, "kind": "oracle", "per_outer_step_s": dt / max(1, info["outer_iters"]),
-            "sample": f"{info['outer_iters']} outer steps of FP64-inner GADI-IR on {WORKLOAD}"}, x, info
+            "sample": f"{info['outer_iters']} outer steps of FP64-inner GADI-IR on {name}"}, x, info
 
 
 def main():
@@ -426,7 +518,11 @@ def main():
     base = {"metric": METRIC, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "data": "synthetic (3D convection-diffusion, manufactured solution)"}
-    cfg = {"workload": WORKLOAD, "n": 262144, "nnz": 1810432, "beta": 100.0, "tol_eta_inf": TOL,
+    from paper_2501_04229_gb300 import problems as P
+    wl = P.WORKLOADS[args.workload]
+    n_wl = wl["N"] ** wl["dim"]
+    nnz_wl = (7 * wl["N"] ** 3 - 6 * wl["N"] ** 2) if wl["dim"] == 3 else (5 * wl["N"] ** 2 - 4 * wl["N"])
+    cfg = {"workload": args.workload, "n": n_wl, "nnz": nnz_wl, "beta": wl["beta"], "tol_eta_inf": TOL,
            "params": args.params, "eps_inner": EPS16,
            "precisions": "u_r=fp16 (fp32 arithmetic), u=u_f=fp64", "kernel": args.kernel,
            "l2": "flushed before every timed step (256 MB write, then read back)",
@@ -434,13 +530,13 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        from paper_2501_04229_gb300 import problems as P
-        p = P.workload(WORKLOAD)
+        p = P.workload(args.workload)
         times = []
         cb = None
         per_step = min(30.0, 180.0 / max(1, args.warmup + args.steps))
         for i in range(args.warmup + args.steps):
-            cb, _, info = cpu_oracle_time(p, args.alpha, args.omega, per_step if i >= args.warmup else 2.0)
+            cb, _, info = cpu_oracle_time(p, args.alpha, args.omega, per_step if i >= args.warmup else 2.0,
+                                          args.workload)
             if i >= args.warmup and cb["value"] is not None:
                 times.append(cb["value"])
             elif i >= args.warmup:
@@ -461,7 +557,7 @@ def main():
     p = r["p"]
     eta_cpu = oracle.backward_error(p.A, p.b, r["x"])
     fwd = float(np.abs(r["x"] - p.x_exact).max())
-    cb, _, _ = cpu_oracle_time(p, args.alpha, args.omega, args.cpu_sample_s)
+    cb, _, _ = cpu_oracle_time(p, args.alpha, args.omega, args.cpu_sample_s, args.workload)
     if cb["value"] is None:
         cb["value"] = cb["per_outer_step_s"] * r["info"]["outer_iters"]
         cb["sample"] += f"; scaled to the GPU run's {r['info']['outer_iters']} outer steps"
@@ -483,6 +579,7 @@ def main():
         "fp64_gadi_same_gpu": r["fp64"],
         "speedup_vs_fp64_gadi": (r["fp64"]["time_s"] / r["value"]) if r["fp64"] else None,
         "spmv": r["spmv"],
+        "hbm_case": r["hbm_case"],
     })
     print(json.dumps(line))
 

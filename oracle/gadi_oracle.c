@@ -28,10 +28,11 @@
  *     FP64 update scalar. The "naive" half mode instead rounds alpha into the
  *     FP16 diagonal and scales nothing, for the paper's unscaled behaviour.
  *
- * Rounding: FP64 products are fused with their sum (C99 fma, one rounding per
- * term), the paper fixing only the precision (u_f = u = double); FP32
- * arithmetic of the low-precision modes rounds every product and sum
- * separately. Compile with -ffp-contract=off so that nothing else is fused.
+ * Rounding: products are fused with their sum (C99 fma / fmaf, one rounding
+ * per term) in FP64 and in the FP32 arithmetic of the low-precision modes,
+ * the paper fixing only the precisions (u_f = u = double, FP32 arithmetic
+ * for u_r = half); a product that starts a sum (sigma x_i) is rounded on its
+ * own. Compile with -ffp-contract=off so that nothing else is fused.
  * Determinism: dot products are summed in fixed blocks of OR_BLK elements and
  * the block sums are added in order, so results do not depend on the number
  * of OpenMP threads.
@@ -318,7 +319,8 @@ int64_t or_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const double *v
 /* ------------------------------------------------------------------ */
 /* Low-precision inner solvers: FP32 arithmetic, storage rounded to the */
 /* inner precision (FP32 itself, or FP16 emulated with _Float16).       */
-/* Every stored value is the result of rnd(); every sum runs in float.  */
+/* Every stored value is the result of rnd(); every sum runs in float,  */
+/* each product-sum as one fused multiply-add (fmaf).                   */
 /* ------------------------------------------------------------------ */
 
 static inline float rnd_store(float x, int half)
@@ -334,7 +336,7 @@ static float dot32(int64_t n, const float *a, const float *b)
     for (int64_t k = 0; k < nb; ++k) {
         int64_t lo = k * OR_BLK, hi = lo + OR_BLK < n ? lo + OR_BLK : n;
         float s = 0.0f;
-        for (int64_t i = lo; i < hi; ++i) s += a[i] * b[i];
+        for (int64_t i = lo; i < hi; ++i) s = fmaf(a[i], b[i], s);
         part[k] = s;
     }
     float s = 0.0f;
@@ -361,7 +363,7 @@ static void spmv32(int64_t n, const int32_t *rp, const int32_t *ci, const float 
     #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         float s = sigma * x[i];
-        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * x[ci[k]];
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = fmaf(v[k], x[ci[k]], s);
         y[i] = rnd_store(s, half);
     }
 }
@@ -386,15 +388,15 @@ static int64_t lp_cg(int64_t n, const int32_t *rp, const int32_t *ci, const floa
             float a = rr / pq;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
             for (int64_t i = 0; i < n; ++i) {
-                z[i] = rnd_store(z[i] + a * p[i], half);
-                r[i] = rnd_store(r[i] - a * q[i], half);
+                z[i] = rnd_store(fmaf(a, p[i], z[i]), half);
+                r[i] = rnd_store(fmaf(-a, q[i], r[i]), half);
             }
             float rrn = dot32(n, r, r);
             if (!isfinite(rrn)) { it = -1; break; }
             if (rrn <= eps2 * rr0) break;
             float beta = rrn / rr;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-            for (int64_t i = 0; i < n; ++i) p[i] = rnd_store(r[i] + beta * p[i], half);
+            for (int64_t i = 0; i < n; ++i) p[i] = rnd_store(fmaf(beta, p[i], r[i]), half);
             rr = rrn;
         }
     }
@@ -427,8 +429,8 @@ static int64_t lp_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const fl
             float a = g / qq;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
             for (int64_t i = 0; i < n; ++i) {
-                y[i] = rnd_store(y[i] + a * p[i], half);
-                r[i] = rnd_store(r[i] - a * q[i], half);
+                y[i] = rnd_store(fmaf(a, p[i], y[i]), half);
+                r[i] = rnd_store(fmaf(-a, q[i], r[i]), half);
             }
             float rr = dot32(n, r, r);
             if (!isfinite(rr)) { it = -1; break; }
@@ -437,7 +439,7 @@ static int64_t lp_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const fl
             float gn = dot32(n, s, s);
             float beta = gn / g;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-            for (int64_t i = 0; i < n; ++i) p[i] = rnd_store(s[i] + beta * p[i], half);
+            for (int64_t i = 0; i < n; ++i) p[i] = rnd_store(fmaf(beta, p[i], s[i]), half);
             g = gn;
         }
     }

@@ -19,12 +19,46 @@ enum : int {
 // ---------------------------------------------------------------------------
 // Precision traits. T is the storage type of the inner vectors and matrix
 // values; Acc the arithmetic type (FP32 for FP16 storage, FP64 otherwise).
-// Every rounding step is the one written in the source: FP32 uses separately
-// rounded multiply and add (no contraction); FP64 uses one fused
-// multiply-add per term (madd), which halves the FP64 instructions on a GPU
-// with a low FP64 rate.
+// Every rounding step is the one written in the source: a sum of products
+// takes one fused multiply-add per term (madd) in FP32 and in FP64, which
+// halves the instructions (and on this GPU's low FP64 rate matters most
+// there); a lone product or sum is rounded on its own.
 // ---------------------------------------------------------------------------
 template <class T> struct Prec;
+
+// Two FP32 values in one 64-bit register pair, operated on by the packed
+// FP32 instructions (mul.rn.f32x2 / fma.rn.f32x2): each lane is an IEEE
+// round-to-nearest-even operation, the same result as the scalar
+// __fmul_rn / __fmaf_rn, at half the instruction count. (A packed multiply
+// followed by a packed add is contracted into a fused multiply-add by the
+// assembler even with .rn, so sums of products are written as fma here and
+// everywhere in the FP32 arithmetic of the FP16 path.)
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+// a b + c per lane
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
 
 template <> struct Prec<__half> {
     using Acc = float;
@@ -38,8 +72,49 @@ template <> struct Prec<__half> {
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-    // c + a b
-    static __device__ __forceinline__ float madd(float c, float a, float b) { return __fadd_rn(c, __fmul_rn(a, b)); }
+    // c + a b, one fused multiply-add (one rounding)
+    static __device__ __forceinline__ float madd(float c, float a, float b) { return __fmaf_rn(a, b, c); }
+    // element-wise, two lanes per packed instruction (outputs may alias inputs):
+    // o = c + a b with a scalar; o = c + a b; o = a b with a scalar
+    template <int K>
+    static __device__ __forceinline__ void madd_s(float (&o)[K], const float (&c)[K], float a, const float (&b)[K])
+    {
+        if constexpr (K % 2 == 0) {
+            const unsigned long long aa = f2_pack(a, a);
+#pragma unroll
+            for (int k = 0; k < K; k += 2)
+                f2_unpack(f2_fma(aa, f2_pack(b[k], b[k + 1]), f2_pack(c[k], c[k + 1])), o[k], o[k + 1]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) o[k] = madd(c[k], a, b[k]);
+        }
+    }
+    template <int K>
+    static __device__ __forceinline__ void madd_v(float (&o)[K], const float (&c)[K], const float (&a)[K],
+                                                  const float (&b)[K])
+    {
+        if constexpr (K % 2 == 0) {
+#pragma unroll
+            for (int k = 0; k < K; k += 2)
+                f2_unpack(f2_fma(f2_pack(a[k], a[k + 1]), f2_pack(b[k], b[k + 1]), f2_pack(c[k], c[k + 1])),
+                          o[k], o[k + 1]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) o[k] = madd(c[k], a[k], b[k]);
+        }
+    }
+    template <int K>
+    static __device__ __forceinline__ void mul_s(float (&o)[K], float a, const float (&b)[K])
+    {
+        if constexpr (K % 2 == 0) {
+            const unsigned long long aa = f2_pack(a, a);
+#pragma unroll
+            for (int k = 0; k < K; k += 2) f2_unpack(f2_mul(aa, f2_pack(b[k], b[k + 1])), o[k], o[k + 1]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) o[k] = mul(a, b[k]);
+        }
+    }
     // round an even number of values through FP16, two per conversion
     template <int K>
     static __device__ __forceinline__ void rndv(float (&v)[K])
@@ -69,6 +144,25 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
     static __device__ __forceinline__ double madd(double c, double a, double b) { return __fma_rn(a, b, c); }
+    template <int K>
+    static __device__ __forceinline__ void madd_s(double (&o)[K], const double (&c)[K], double a, const double (&b)[K])
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) o[k] = madd(c[k], a, b[k]);
+    }
+    template <int K>
+    static __device__ __forceinline__ void madd_v(double (&o)[K], const double (&c)[K], const double (&a)[K],
+                                                  const double (&b)[K])
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) o[k] = madd(c[k], a[k], b[k]);
+    }
+    template <int K>
+    static __device__ __forceinline__ void mul_s(double (&o)[K], double a, const double (&b)[K])
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) o[k] = mul(a, b[k]);
+    }
     template <int K>
     static __device__ __forceinline__ void rndv(double (&)[K]) {}
 };

@@ -12,10 +12,10 @@
 // per item).
 //
 // A row is evaluated as sigma*f(i) first, then the matrix entries in
-// ascending column order (the CSR order). Inner precision FP16: products of
-// two FP16 values are exact in FP32, sums are explicitly rounded FP32 adds.
-// FP64 (residual, FP64 inner path): each term is one fused multiply-add.
-// So a row equals, bit for bit, the same sum formed on the CPU.
+// ascending column order (the CSR order), each term one fused multiply-add:
+// in FP32 for the FP16 inner precision, in FP64 for the residual and the
+// FP64 inner path. So a row equals, bit for bit, the same sum formed on the
+// CPU.
 //
 // The vector argument is an expression object with one(j) (value at column
 // j) and many<K>(j0, out) (values at j0..j0+K-1, j0 a multiple of K); the kernel
@@ -173,8 +173,7 @@ struct XAxpy {                       // fl(a + c b)
         Acc x[K], y[K];
         ldv<K>(a, j0, x);
         ldv<K>(b, j0, y);
-#pragma unroll
-        for (int k = 0; k < K; ++k) o[k] = P::madd(x[k], c, y[k]);
+        P::madd_s(o, x, c, y);
         P::rndv(o);
     }
 };
@@ -197,11 +196,9 @@ struct XAxpy2 {                      // fl(a - c fl(b + d e))  (C-G residual upd
         ldv<K>(a, j0, x);
         ldv<K>(b, j0, y);
         ldv<K>(e, j0, w);
-#pragma unroll
-        for (int k = 0; k < K; ++k) w[k] = P::madd(y[k], d, w[k]);
+        P::madd_s(w, y, d, w);
         P::rndv(w);
-#pragma unroll
-        for (int k = 0; k < K; ++k) o[k] = P::madd(x[k], -c, w[k]);
+        P::madd_s(o, x, -c, w);
         P::rndv(o);
     }
 };
@@ -218,8 +215,7 @@ struct XScale {                      // fl(c a): c a power of two, or (2-w) a in
     {
         Acc x[K];
         ldv<K>(a, j0, x);
-#pragma unroll
-        for (int k = 0; k < K; ++k) o[k] = P::mul(x[k], c);
+        P::mul_s(o, c, x);
         P::rndv(o);
     }
 };
@@ -259,8 +255,7 @@ struct XDemoteOdd {
     {
         float x[K];
         ldv<K>(r32, j0, x);
-#pragma unroll
-        for (int k = 0; k < K; ++k) x[k] = __fmul_rn(x[k], sc);
+        Prec<__half>::mul_s(x, sc, x);
         Prec<__half>::rndv(x);
 #pragma unroll
         for (int k = 0; k < K; ++k) o[k] = x[k];
@@ -491,92 +486,97 @@ struct StencilOp {
         if constexpr (R == 1) {
             out[0] = row1(which, item, f);
         } else {
+            // element-wise over the item's R rows (packed pairs for FP16); the
+            // x neighbours are the item's own values shifted by one, with a
+            // zero term (value 0, so the sum keeps its value) where a row has
+            // no neighbour
             const int64_t i0 = item * R;
             unsigned cd[3];
             coords(i0, cd);
             const unsigned last = (unsigned)N - 1;
-            Acc c[R], acc[R], t[R], cf[R];
+            Acc c[R], acc[R], t[R], cf[R], sh[R];
             f.template many<R>(i0, c);
             if (which == kOpH) {
                 const bool face = HD != nullptr;
-#pragma unroll
-                for (int k = 0; k < R; ++k) acc[k] = P::mul(sigH, c[k]);
+                P::mul_s(acc, sigH, c);
 #pragma unroll
                 for (int d = DIM - 1; d >= 1; --d)
                     if (cd[d] > 0) {
                         f.template many<R>(i0 - stride(d), t);
-                        if (face) ldv<R>(HK[d], i0 - stride(d), cf);
-#pragma unroll
-                        for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], face ? cf[k] : h_off, t[k]);
+                        if (face) {
+                            ldv<R>(HK[d], i0 - stride(d), cf);
+                            P::madd_v(acc, acc, cf, t);
+                        } else {
+                            P::madd_s(acc, acc, h_off, t);
+                        }
                     }
                 {   // x lower: coupling of node i with i-1 is HK[0][i-1]
                     const Acc xm = cd[0] > 0 ? f.one(i0 - 1) : Acc(0);
-                    Acc c0 = h_off;
-                    if (face) {
-                        ldv<R>(HK[0], i0, cf);
-                        c0 = cd[0] > 0 ? P::ld(HK[0][i0 - 1]) : Acc(0);
-                    }
 #pragma unroll
-                    for (int k = 0; k < R; ++k)
-                        if (k > 0 || cd[0] > 0)
-                            acc[k] = P::madd(acc[k], face ? (k ? cf[k - 1] : c0) : h_off, k ? c[k - 1] : xm);
+                    for (int k = 0; k < R; ++k) sh[k] = k ? c[k - 1] : xm;
+                    if (face) {
+                        Acc cs[R];
+                        ldv<R>(HK[0], i0, cf);
+                        cs[0] = cd[0] > 0 ? P::ld(HK[0][i0 - 1]) : Acc(0);
+#pragma unroll
+                        for (int k = 1; k < R; ++k) cs[k] = cf[k - 1];
+                        P::madd_v(acc, acc, cs, sh);
+                    } else {
+                        P::madd_s(acc, acc, h_off, sh);
+                    }
                 }
                 if (face) {
                     Acc dg[R];
                     ldv<R>(HD, i0, dg);
-#pragma unroll
-                    for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], dg[k], c[k]);
+                    P::madd_v(acc, acc, dg, c);
                 } else {
-#pragma unroll
-                    for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], h_diag, c[k]);
+                    P::madd_s(acc, acc, h_diag, c);
                 }
                 {   // x upper: coupling HK[0][i]
                     const Acc xp = cd[0] + R <= last ? f.one(i0 + R) : Acc(0);
 #pragma unroll
-                    for (int k = 0; k < R; ++k)
-                        if (k < R - 1 || cd[0] + R <= last)
-                            acc[k] = P::madd(acc[k], face ? cf[k] : h_off, k < R - 1 ? c[k + 1] : xp);
+                    for (int k = 0; k < R; ++k) sh[k] = k < R - 1 ? c[k + 1] : xp;
+                    if (face) P::madd_v(acc, acc, cf, sh);
+                    else P::madd_s(acc, acc, h_off, sh);
                 }
 #pragma unroll
                 for (int d = 1; d < DIM; ++d)
                     if (cd[d] < last) {
                         f.template many<R>(i0 + stride(d), t);
-                        if (face) ldv<R>(HK[d], i0, cf);
-#pragma unroll
-                        for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], face ? cf[k] : h_off, t[k]);
+                        if (face) {
+                            ldv<R>(HK[d], i0, cf);
+                            P::madd_v(acc, acc, cf, t);
+                        } else {
+                            P::madd_s(acc, acc, h_off, t);
+                        }
                     }
             } else {
                 const Acc lo = which == kOpS ? -s_c : s_c;
-#pragma unroll
-                for (int k = 0; k < R; ++k) acc[k] = P::mul(sigS, c[k]);
+                P::mul_s(acc, sigS, c);
 #pragma unroll
                 for (int d = DIM - 1; d >= 1; --d)
                     if (cd[d] > 0) {
                         f.template many<R>(i0 - stride(d), t);
-#pragma unroll
-                        for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], lo, t[k]);
+                        P::madd_s(acc, acc, lo, t);
                     }
                 {
                     const Acc xm = cd[0] > 0 ? f.one(i0 - 1) : Acc(0);
 #pragma unroll
-                    for (int k = 0; k < R; ++k)
-                        if (k > 0 || cd[0] > 0) acc[k] = P::madd(acc[k], lo, k ? c[k - 1] : xm);
+                    for (int k = 0; k < R; ++k) sh[k] = k ? c[k - 1] : xm;
+                    P::madd_s(acc, acc, lo, sh);
                 }
-                if (s_diag != Acc(0))
-#pragma unroll
-                    for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], s_diag, c[k]);
+                if (s_diag != Acc(0)) P::madd_s(acc, acc, s_diag, c);
                 {
                     const Acc xp = cd[0] + R <= last ? f.one(i0 + R) : Acc(0);
 #pragma unroll
-                    for (int k = 0; k < R; ++k)
-                        if (k < R - 1 || cd[0] + R <= last) acc[k] = P::madd(acc[k], -lo, k < R - 1 ? c[k + 1] : xp);
+                    for (int k = 0; k < R; ++k) sh[k] = k < R - 1 ? c[k + 1] : xp;
+                    P::madd_s(acc, acc, -lo, sh);
                 }
 #pragma unroll
                 for (int d = 1; d < DIM; ++d)
                     if (cd[d] < last) {
                         f.template many<R>(i0 + stride(d), t);
-#pragma unroll
-                        for (int k = 0; k < R; ++k) acc[k] = P::madd(acc[k], -lo, t[k]);
+                        P::madd_s(acc, acc, -lo, t);
                     }
             }
 #pragma unroll

@@ -214,20 +214,14 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
                         } else {
                             IO::ld(p, it, p_);
                             IO::ld(sc, it, s_);
-#pragma unroll
-                            for (int q = 0; q < R; ++q) {
-                                p_[q] = P::madd(r_[q], be, p_[q]);
-                                s_[q] = P::madd(u_[q], be, s_[q]);
-                            }
+                            P::madd_s(p_, r_, be, p_);
+                            P::madd_s(s_, u_, be, s_);
                             P::rndv(p_);
                             P::rndv(s_);
                         }
                         op.rows(kOpH, it, frn, unew);
-#pragma unroll
-                        for (int q = 0; q < R; ++q) {
-                            z_[q] = P::madd(z_[q], al, p_[q]);
-                            rnew[q] = P::madd(r_[q], -al, s_[q]);
-                        }
+                        P::madd_s(z_, z_, al, p_);
+                        P::madd_s(rnew, r_, -al, s_);
                         P::rndv(z_);
                         P::rndv(rnew);
                         P::rndv(unew);
@@ -366,8 +360,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
                         if constexpr (R > 1) frs.template many<R>(it * R, rn_);
                         else rn_[0] = frs.one(it);
                         op.rows(kOpST, it, frs, ss);
-#pragma unroll
-                        for (int j = 0; j < R; ++j) yy[j] = P::madd(yy[j], ac, pp[j]);
+                        P::madd_s(yy, yy, ac, pp);
                         P::rndv(yy);
                         P::rndv(ss);
 #pragma unroll

@@ -239,6 +239,9 @@ WORKLOADS = {
     "convdiff3d_64_b100": dict(dim=3, N=64, beta=100.0, rhs="manufactured"),
     # 3D 128^3, beta = 50, GRF face coefficients (seed 3), manufactured solution
     "convdiff3d_128_b50_grf": dict(dim=3, N=128, beta=50.0, rhs="manufactured", grf_seed=3),
+    # 3D 192^3, beta = 100, manufactured solution: the working set (about 0.5 GB)
+    # is several times the 129 MB L2, so the inner sweeps stream from HBM
+    "convdiff3d_192_b100": dict(dim=3, N=192, beta=100.0, rhs="manufactured"),
 }
 
 
