@@ -133,19 +133,23 @@ GADI_API gadi_status gadi_create(const gadi_csr *A, gadi_splitting split, const 
                         const gadi_stencil *structure, void *cuda_stream, gadi_solver **out);
 
 /* Parameters of eq. (gadi) and the precision triple of Algorithm 1.
- * alpha > 0 and omega in [0, 2) (Thm 1). Supported: u = u_f = GADI_F64 and
- * u_r in {GADI_F16, GADI_F64}; other valid triples return UNSUPPORTED.
+ * alpha > 0 and omega in [0, 2) (Thm 1). Supported: u = u_f = GADI_F64 with
+ * any u_r; other valid triples return UNSUPPORTED.
  * u_r = GADI_F16 means FP16 storage of the inner matrix values and vectors
- * with FP32 arithmetic; A, r and z are scaled by powers of two so FP16 stays
- * in range, and (2 - omega) alpha is applied in the FP64 update.
- * u_r = GADI_F64 with the default inner tolerance is plain FP64 GADI. */
+ * with FP32 arithmetic (one fused multiply-add per product-sum); A, r and z
+ * are scaled by powers of two so FP16 stays in range, and (2 - omega) alpha
+ * is applied in the FP64 update. u_r = GADI_BF16: the same with bfloat16
+ * storage (8 significant bits). u_r = GADI_F32: FP32 storage and arithmetic,
+ * r and z scaled, the operators not. u_r = GADI_F64 with the default inner
+ * tolerance is plain FP64 GADI. */
 GADI_API gadi_status gadi_set_params(gadi_solver *h, double alpha, double omega,
                             gadi_precision u_r, gadi_precision u, gadi_precision u_f);
 
 /* Inner relative tolerance eps (0 < eps < 1): each inner solve stops when
  * ||rhs - K v||_2 <= eps ||rhs||_2, or after max_inner iterations (>= 1).
- * max_outer (>= 0) caps the refinement steps. Defaults: eps 1e-2 (FP16
- * inner) / 1e-10 (FP64 inner), max_inner 200, max_outer 100000. */
+ * max_outer (>= 0) caps the refinement steps. Defaults: eps 1e-2 (inner
+ * precision below FP64) / 1e-10 (FP64 inner), max_inner 200, max_outer
+ * 100000. */
 GADI_API gadi_status gadi_set_inner(gadi_solver *h, double eps_inner, int32_t max_inner, int32_t max_outer);
 
 /* Stopping criterion kind for gadi_solve's tol (default GADI_STOP_ETA). */
@@ -209,7 +213,8 @@ GADI_API gadi_status gadi_solve(gadi_solver *h, const double *b, double *x, doub
  *   2: K = S' = 2^-sN (aI + N)
  *   3: K = S'^T
  * x, y are device pointers of n elements of the inner precision (FP64 for
- * which = 0). Asynchronous on the handle's stream. */
+ * which = 0; FP16, bfloat16, FP32 or FP64 after gadi_set_params' u_r).
+ * Asynchronous on the handle's stream. */
 GADI_API gadi_status gadi_apply(gadi_solver *h, int32_t which, const void *x, void *y);
 
 /* Scale exponents (sM, sN) that the inner operators use for the current

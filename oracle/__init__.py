@@ -27,7 +27,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PREC_DOUBLE, PREC_SINGLE, PREC_HALF, PREC_HALF_NAIVE = 0, 1, 2, 3
+PREC_DOUBLE, PREC_SINGLE, PREC_HALF, PREC_HALF_NAIVE, PREC_BF16 = 0, 1, 2, 3, 4
 STOP_ETA, STOP_RES = 0, 1
 OK, INVALID, OOM, NOT_CONVERGED, DIVERGED = 0, 1, 2, 5, 6
 
@@ -89,6 +89,7 @@ def _load():
         "or_lp_apply": (C.c_int, [i64, p_i32, p_i32, p_f64, p_f64, f64, C.c_int, C.c_int,
                                   p_f64, p_f64, p_i32, p_i32]),
         "or_to_half_bits": (None, [i64, p_f64, p_u16]),
+        "or_to_bf16_bits": (None, [i64, p_f64, p_u16]),
         "or_wtime": (f64, []),
     }
     for name, (res, args) in sig.items():
@@ -255,6 +256,14 @@ def lp_apply(A, alpha, which, prec, x, m_user=None):
     if st != OK:
         raise ValueError("or_lp_apply failed")
     return y, sM.value, sN.value
+
+
+def to_bf16_bits(x) -> np.ndarray:
+    """bfloat16 bit patterns of fl_bf16(x), round-to-nearest-even from FP64."""
+    x = _f64(x)
+    out = np.empty(x.shape, dtype=np.uint16)
+    _load().or_to_bf16_bits(x.size, _p(x, C.c_double), _p(out, C.c_uint16))
+    return out
 
 
 def to_half_bits(x) -> np.ndarray:

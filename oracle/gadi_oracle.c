@@ -21,6 +21,8 @@
  *     inner initial residual), with an iteration cap;
  *   - residual sign r = b - Ax; start x0 given by the caller (zero in the
  *     paper's experiments);
+ *   - bfloat16 inner precision: as FP16 (scaled the same way), with 8
+ *     significant bits and FP32's exponent range;
  *   - FP16 inner precision ("half"): FP16 storage of matrix values and inner
  *     vectors, FP32 arithmetic; the matrix, the residual and the first
  *     correction are scaled by powers of two so that FP16 stays in range; the
@@ -55,7 +57,7 @@
 /* loops over fewer elements than this run on one thread */
 #define OR_PAR_MIN 32768
 
-enum { OR_PREC_DOUBLE = 0, OR_PREC_SINGLE = 1, OR_PREC_HALF = 2, OR_PREC_HALF_NAIVE = 3 };
+enum { OR_PREC_DOUBLE = 0, OR_PREC_SINGLE = 1, OR_PREC_HALF = 2, OR_PREC_HALF_NAIVE = 3, OR_PREC_BF16 = 4 };
 enum { OR_STOP_ETA = 0, OR_STOP_RES = 1 };
 
 typedef struct {
@@ -318,14 +320,56 @@ int64_t or_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const double *v
 
 /* ------------------------------------------------------------------ */
 /* Low-precision inner solvers: FP32 arithmetic, storage rounded to the */
-/* inner precision (FP32 itself, or FP16 emulated with _Float16).       */
+/* inner precision (FP32 itself, FP16 emulated with _Float16, or        */
+/* bfloat16 emulated by rounding FP32 bit patterns).                     */
 /* Every stored value is the result of rnd(); every sum runs in float,  */
 /* each product-sum as one fused multiply-add (fmaf).                   */
 /* ------------------------------------------------------------------ */
 
-static inline float rnd_store(float x, int half)
+/* Storage rounding of the low-precision modes: rt = 0 FP32 (none), 1 FP16,
+ * 2 bfloat16 (8 significant bits, FP32's exponent range), all round to
+ * nearest even. */
+enum { RT_F32 = 0, RT_F16 = 1, RT_BF16 = 2 };
+
+static inline float bf16_of_float(float x)
 {
-    return half ? (float)(_Float16)x : x;
+    uint32_t u;
+    memcpy(&u, &x, sizeof u);
+    if ((u & 0x7f800000u) == 0x7f800000u) {
+        if (u & 0x7fffffu) u |= 0x400000u;            /* NaN stays (quiet) NaN */
+        u &= 0xffff0000u;
+    } else {
+        u += 0x7fffu + ((u >> 16) & 1u);              /* nearest, ties to even; overflow -> inf */
+        u &= 0xffff0000u;
+    }
+    memcpy(&x, &u, sizeof x);
+    return x;
+}
+
+/* x rounded to FP32 with round-to-odd: truncated toward zero, last bit set
+ * when inexact. Rounding that to bfloat16 (round to nearest even) equals
+ * rounding x directly, since 24 >= 8 + 2 significant bits. */
+static inline float float_round_odd(double x)
+{
+    float t = (float)x;
+    if (!(x == x) || (double)t == x) return t;
+    if (fabs((double)t) > fabs(x)) t = nextafterf(t, 0.0f);
+    uint32_t u;
+    memcpy(&u, &t, sizeof u);
+    u |= 1u;
+    memcpy(&t, &u, sizeof t);
+    return t;
+}
+
+static inline float rnd_store(float x, int rt)
+{
+    return rt == RT_F16 ? (float)(_Float16)x : (rt == RT_BF16 ? bf16_of_float(x) : x);
+}
+
+/* an FP64 value rounded once to the storage precision */
+static inline float rnd_from64(double v, int rt)
+{
+    return rt == RT_F16 ? (float)(_Float16)v : (rt == RT_BF16 ? bf16_of_float(float_round_odd(v)) : (float)v);
 }
 
 static float dot32(int64_t n, const float *a, const float *b)
@@ -358,19 +402,19 @@ static float norm_inf32(int64_t n, const float *a)
 
 /* y = rnd(sigma x + V x), V values already rounded to storage precision */
 static void spmv32(int64_t n, const int32_t *rp, const int32_t *ci, const float *v,
-                   float sigma, const float *x, float *y, int half)
+                   float sigma, const float *x, float *y, int rt)
 {
     #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         float s = sigma * x[i];
         for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = fmaf(v[k], x[ci[k]], s);
-        y[i] = rnd_store(s, half);
+        y[i] = rnd_store(s, rt);
     }
 }
 
 /* CG on (sigma I + M) z = rhs from z = 0, low precision. */
 static int64_t lp_cg(int64_t n, const int32_t *rp, const int32_t *ci, const float *m, float sigma,
-                     const float *rhs, float *z, double eps, int32_t maxit, int half)
+                     const float *rhs, float *z, double eps, int32_t maxit, int rt)
 {
     size_t sz = (size_t)(n > 0 ? n : 1) * sizeof(float);
     float *r = (float *)malloc(sz), *p = (float *)malloc(sz), *q = (float *)malloc(sz);
@@ -381,22 +425,22 @@ static int64_t lp_cg(int64_t n, const int32_t *rp, const int32_t *ci, const floa
     int64_t it = 0;
     if (rr0 > 0.0f) {
         while (it < maxit) {
-            spmv32(n, rp, ci, m, sigma, p, q, half);
+            spmv32(n, rp, ci, m, sigma, p, q, rt);
             ++it;
             float pq = dot32(n, p, q);
             if (!(pq > 0.0f) || !isfinite(pq)) { it = -1; break; }
             float a = rr / pq;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
             for (int64_t i = 0; i < n; ++i) {
-                z[i] = rnd_store(fmaf(a, p[i], z[i]), half);
-                r[i] = rnd_store(fmaf(-a, q[i], r[i]), half);
+                z[i] = rnd_store(fmaf(a, p[i], z[i]), rt);
+                r[i] = rnd_store(fmaf(-a, q[i], r[i]), rt);
             }
             float rrn = dot32(n, r, r);
             if (!isfinite(rrn)) { it = -1; break; }
             if (rrn <= eps2 * rr0) break;
             float beta = rrn / rr;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-            for (int64_t i = 0; i < n; ++i) p[i] = rnd_store(fmaf(beta, p[i], r[i]), half);
+            for (int64_t i = 0; i < n; ++i) p[i] = rnd_store(fmaf(beta, p[i], r[i]), rt);
             rr = rrn;
         }
     }
@@ -407,7 +451,7 @@ static int64_t lp_cg(int64_t n, const int32_t *rp, const int32_t *ci, const floa
 /* CGNR on (sigma I + N) y = rhs from y = 0, low precision. */
 static int64_t lp_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const float *nv,
                        const int32_t *rpt, const int32_t *cit, const float *nvt, float sigma,
-                       const float *rhs, float *y, double eps, int32_t maxit, int half)
+                       const float *rhs, float *y, double eps, int32_t maxit, int rt)
 {
     size_t sz = (size_t)(n > 0 ? n : 1) * sizeof(float);
     float *r = (float *)malloc(sz), *s = (float *)malloc(sz);
@@ -418,28 +462,28 @@ static int64_t lp_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const fl
     float eps2 = (float)(eps * eps);
     int64_t it = 0;
     if (rr0 > 0.0f) {
-        spmv32(n, rpt, cit, nvt, sigma, r, s, half);
+        spmv32(n, rpt, cit, nvt, sigma, r, s, rt);
         memcpy(p, s, sz);
         float g = dot32(n, s, s);
         while (it < maxit) {
-            spmv32(n, rp, ci, nv, sigma, p, q, half);
+            spmv32(n, rp, ci, nv, sigma, p, q, rt);
             ++it;
             float qq = dot32(n, q, q);
             if (!(qq > 0.0f) || !isfinite(qq)) { it = -1; break; }
             float a = g / qq;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
             for (int64_t i = 0; i < n; ++i) {
-                y[i] = rnd_store(fmaf(a, p[i], y[i]), half);
-                r[i] = rnd_store(fmaf(-a, q[i], r[i]), half);
+                y[i] = rnd_store(fmaf(a, p[i], y[i]), rt);
+                r[i] = rnd_store(fmaf(-a, q[i], r[i]), rt);
             }
             float rr = dot32(n, r, r);
             if (!isfinite(rr)) { it = -1; break; }
             if (rr <= eps2 * rr0) break;
-            spmv32(n, rpt, cit, nvt, sigma, r, s, half);
+            spmv32(n, rpt, cit, nvt, sigma, r, s, rt);
             float gn = dot32(n, s, s);
             float beta = gn / g;
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-            for (int64_t i = 0; i < n; ++i) p[i] = rnd_store(fmaf(beta, p[i], s[i]), half);
+            for (int64_t i = 0; i < n; ++i) p[i] = rnd_store(fmaf(beta, p[i], s[i]), rt);
             g = gn;
         }
     }
@@ -586,7 +630,7 @@ int or_gadi_ir_split(int64_t n, const int32_t *rp, const int32_t *ci, const doub
                      or_info *info, double *eta_hist, int32_t *itH, int32_t *itS)
 {
     memset(info, 0, sizeof(*info));
-    if (check_params(P) != OR_OK || P->inner_prec < 0 || P->inner_prec > 3) {
+    if (check_params(P) != OR_OK || P->inner_prec < 0 || P->inner_prec > OR_PREC_BF16) {
         info->status = OR_INVALID; return OR_INVALID;
     }
     int64_t nnz = rp[n];
@@ -603,8 +647,10 @@ int or_gadi_ir_split(int64_t n, const int32_t *rp, const int32_t *ci, const doub
     transpose_csr(n, rp, ci, nv, &rpt, &cit, &nvt);
     const double al = P->alpha, om = P->omega, pfac = (2.0 - om) * al;
     const int prec = P->inner_prec;
-    const int half = (prec == OR_PREC_HALF || prec == OR_PREC_HALF_NAIVE);
     const int naive = (prec == OR_PREC_HALF_NAIVE);
+    /* storage rounding; the FP16 and bfloat16 modes scale the operators */
+    const int rt = (prec == OR_PREC_HALF || naive) ? RT_F16 : (prec == OR_PREC_BF16 ? RT_BF16 : RT_F32);
+    const int half = (rt != RT_F32);
 
     double *r = (double *)malloc(szv), *z = (double *)malloc(szv), *y = (double *)malloc(szv);
     /* low-precision copies */
@@ -639,9 +685,9 @@ int or_gadi_ir_split(int64_t n, const int32_t *rp, const int32_t *ci, const doub
                 if (sNt > sN) sN = sNt;     /* one scale for S and S^T */
             }
             for (int64_t k = 0; k < nnz; ++k) {
-                mf[k] = half ? (float)(_Float16)ldexp(m[k], -sM) : (float)m[k];
-                nf[k] = half ? (float)(_Float16)ldexp(nv[k], -sN) : (float)nv[k];
-                nft[k] = half ? (float)(_Float16)ldexp(nvt[k], -sN) : (float)nvt[k];
+                mf[k] = rnd_from64(ldexp(m[k], -sM), rt);
+                nf[k] = rnd_from64(ldexp(nv[k], -sN), rt);
+                nft[k] = rnd_from64(ldexp(nvt[k], -sN), rt);
             }
             sigH = (float)ldexp(al, -sM);
             sigS = (float)ldexp(al, -sN);
@@ -687,24 +733,24 @@ int or_gadi_ir_split(int64_t n, const int32_t *rp, const int32_t *ci, const doub
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
             for (int64_t i = 0; i < n; ++i) {
                 double v = ldexp(r[i], -e);
-                rf[i] = half ? (float)(_Float16)v : (float)v;
+                rf[i] = rnd_from64(v, rt);
             }
-            ih = lp_cg(n, rp, ci, mf, sigH, rf, zf, P->eps_inner, P->max_inner, half);
+            ih = lp_cg(n, rp, ci, mf, sigH, rf, zf, P->eps_inner, P->max_inner, rt);
             if (ih < 0) { status = OR_DIVERGED; break; }
             if (naive) {
                 /* (2-w) a z formed in the inner precision */
                 float pf = (float)pfac;
                 #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-                for (int64_t i = 0; i < n; ++i) zf[i] = rnd_store(pf * zf[i], half);
+                for (int64_t i = 0; i < n; ++i) zf[i] = rnd_store(pf * zf[i], rt);
                 upd = 1.0;
             } else {
                 float zinf = norm_inf32(n, zf);
                 if (zinf > 0.0f && isfinite(zinf)) ez = ilog2_floor((double)zinf);
                 #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
-                for (int64_t i = 0; i < n; ++i) zf[i] = rnd_store(ldexpf(zf[i], -ez), half);
+                for (int64_t i = 0; i < n; ++i) zf[i] = rnd_store(ldexpf(zf[i], -ez), rt);
                 upd = ldexp(pfac, e - sM + ez - sN);
             }
-            is = lp_cgnr(n, rp, ci, nf, rpt, cit, nft, sigS, zf, yf, P->eps_inner, P->max_inner, half);
+            is = lp_cgnr(n, rp, ci, nf, rpt, cit, nft, sigS, zf, yf, P->eps_inner, P->max_inner, rt);
             if (is < 0) { status = OR_DIVERGED; break; }
             /* step 4 in u = FP64 */
             #pragma omp parallel for schedule(static) if (n > OR_PAR_MIN)
@@ -756,8 +802,9 @@ int or_lp_apply(int64_t n, const int32_t *rp, const int32_t *ci, const double *a
     }
     int32_t *rpt, *cit; double *nvt;
     transpose_csr(n, rp, ci, nv, &rpt, &cit, &nvt);
-    const int half = prec == OR_PREC_HALF || prec == OR_PREC_HALF_NAIVE;
     const int naive = prec == OR_PREC_HALF_NAIVE;
+    const int rt = (prec == OR_PREC_HALF || naive) ? RT_F16 : (prec == OR_PREC_BF16 ? RT_BF16 : RT_F32);
+    const int half = rt != RT_F32;
     int sM = 0, sN = 0;
     if (half && !naive) {
         sM = half_scale_exponent(n, rp, m, alpha);
@@ -784,12 +831,12 @@ int or_lp_apply(int64_t n, const int32_t *rp, const int32_t *ci, const double *a
             for (int32_t k = rpx[i]; k < rpx[i + 1]; ++k) {
                 /* naive: alpha rounded into the stored diagonal, nothing scaled */
                 double v = naive ? src[k] + (cix[k] == i ? alpha : 0.0) : ldexp(src[k], -s);
-                vf[k] = half ? (float)(_Float16)v : (float)src[k];
+                vf[k] = half ? rnd_from64(v, rt) : (float)src[k];
             }
         for (int64_t i = 0; i < n; ++i) xf[i] = (float)x[i];
         float sig = naive ? 0.0f : (float)ldexp(alpha, -s);
-        if (which == 3) spmv32(n, rpt, cit, vf, sig, xf, yf, half);
-        else spmv32(n, rp, ci, vf, sig, xf, yf, half);
+        if (which == 3) spmv32(n, rpt, cit, vf, sig, xf, yf, rt);
+        else spmv32(n, rp, ci, vf, sig, xf, yf, rt);
         for (int64_t i = 0; i < n; ++i) y[i] = (double)yf[i];
         free(vf); free(xf); free(yf);
     }
@@ -804,6 +851,17 @@ void or_to_half_bits(int64_t n, const double *in, uint16_t *out)
     for (int64_t i = 0; i < n; ++i) {
         _Float16 h = (_Float16)in[i];
         memcpy(&out[i], &h, sizeof(uint16_t));
+    }
+}
+
+/* FP64 -> bfloat16 (round to nearest even, one rounding), as raw bits. */
+void or_to_bf16_bits(int64_t n, const double *in, uint16_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float f = bf16_of_float(float_round_odd(in[i]));
+        uint32_t u;
+        memcpy(&u, &f, sizeof u);
+        out[i] = (uint16_t)(u >> 16);
     }
 }
 

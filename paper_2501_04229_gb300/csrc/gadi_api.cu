@@ -133,19 +133,21 @@ __global__ void k_split_ell(int64_t n, const int *rp, const int *ci, const doubl
     }
 }
 
-// dst = fl16(src * 2^-s), round to nearest even, directly from FP64
-__global__ void k_demote(int64_t cnt, const double *src, __half *dst, double scale)
+// dst = fl_T(src * 2^-s), round to nearest even, directly from FP64
+template <class TD>
+__global__ void k_demote(int64_t cnt, const double *src, TD *dst, double scale)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = __double2half(__dmul_rn(src[i], scale));
+        dst[i] = Prec<TD>::from64(__dmul_rn(src[i], scale));
 }
 
 // unscaled FP16 mode: dst = fl16(sign src + alpha) on the stored diagonal
 // (the first slot of a row whose column is the row; padding slots come after
 // the row's entries), fl16(sign src) elsewhere. W = 0: every entry is a
 // diagonal. sign = -1 forms N^T = -N of a skew-symmetric N.
-__global__ void k_demote_diag(int64_t cnt, int W, const int *col, const double *src, __half *dst,
+template <class TD>
+__global__ void k_demote_diag(int64_t cnt, int W, const int *col, const double *src, TD *dst,
                               double alpha, double sign)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
@@ -158,15 +160,16 @@ __global__ void k_demote_diag(int64_t cnt, int W, const int *col, const double *
                 if (col[k] == row) diag = false;
         }
         const double v = sign < 0.0 ? -src[i] : src[i];
-        dst[i] = __double2half(diag ? __dadd_rn(v, alpha) : v);
+        dst[i] = Prec<TD>::from64(diag ? __dadd_rn(v, alpha) : v);
     }
 }
 
-__global__ void k_count_range(int64_t cnt, const double *src, const __half *dst, int *lost)
+template <class TD>
+__global__ void k_count_range(int64_t cnt, const double *src, const TD *dst, int *lost)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float h = __half2float(dst[i]);
+        float h = Prec<TD>::ld(dst[i]);
         if ((src[i] != 0.0 && h == 0.0f) || isinf(h)) atomicAdd(lost, 1);
     }
 }
@@ -269,7 +272,9 @@ struct gadi_solver {
     // ELL arrays (device)
     int *ecol = nullptr;
     double *ea = nullptr, *em = nullptr, *en = nullptr, *ent = nullptr;
+    // 2-byte inner values (FP16, or bfloat16 in the same arrays) and FP32 ones
     __half *m16 = nullptr, *n16 = nullptr, *nt16 = nullptr;
+    float *m32 = nullptr, *n32 = nullptr, *nt32 = nullptr;
     double anorm = 0, mnorm = 0, nnorm = 0, ntnorm = 0;
     // stencil
     bool has_stencil = false;
@@ -281,6 +286,7 @@ struct gadi_solver {
     double a_diag = 0, a_lo = 0, a_hi = 0, m_off = 0, n_up = 0;
     double *AD = nullptr, *AL[3] = {}, *AU[3] = {}, *HD64 = nullptr, *HK64[3] = {};
     __half *HD16 = nullptr, *HK16[3] = {};
+    float *HD32 = nullptr, *HK32[3] = {};
     // parameters
     double alpha = 1.0, omega = 1.0;
     int u_r = GADI_F16;
@@ -298,6 +304,7 @@ struct gadi_solver {
     double demoted_alpha = 0.0;
     int scaling = 1;          // 0: unscaled FP16 inner mode (alpha rounded into the FP16 diagonal)
     int demoted_scaling = 1;
+    int demoted_ur = -1;
     // work
     double *bdev = nullptr, *xdev = nullptr, *r64 = nullptr;
     double *x2 = nullptr;     // second iterate buffer (the iterates alternate with x)
@@ -362,7 +369,8 @@ void release(gadi_solver *h)
     void *ptrs[] = {h->ecol, h->ea, h->em, h->en, h->ent, h->m16, h->n16, h->nt16, h->AD,
                     h->AL[0], h->AL[1], h->AL[2], h->AU[0], h->AU[1], h->AU[2], h->HD64,
                     h->HK64[0], h->HK64[1], h->HK64[2], h->HD16, h->HK16[0], h->HK16[1],
-                    h->HK16[2], h->bdev, h->xdev, h->x2, h->r64, h->vec, h->part, h->ctl, h->scratch};
+                    h->HK16[2], h->bdev, h->xdev, h->x2, h->r64, h->vec, h->part, h->ctl, h->scratch,
+                    h->m32, h->n32, h->nt32, h->HD32, h->HK32[0], h->HK32[1], h->HK32[2]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -398,69 +406,109 @@ bool use_stencil(const gadi_solver *h)
     return h->has_stencil;
 }
 
-// Demote the inner operators for the current alpha (FP16 inner precision).
-gadi_status prepare_inner(gadi_solver *h)
+// The inner operator values of storage type TD, demoted from FP64: scaled by
+// 2^-sM / 2^-sN, or (unscaled FP16 mode) with alpha rounded into the stored
+// diagonals and N^T in its own array.
+template <class TD>
+void demote_all(gadi_solver *h, TD *m, TD *nv, TD *nt, TD *hd, TD *const *hk, bool naive, double scM, double scN)
 {
-    if (h->u_r != GADI_F16) {
-        h->sM = h->sNs = 0;
-        return GADI_OK;
-    }
-    const bool naive = h->scaling == 0;
-    int sM = naive ? 0 : half_scale_exponent(h->mnorm, h->alpha);
-    int sN = naive ? 0 : half_scale_exponent(h->nnorm, h->alpha);
-    if (h->demoted && sM == h->sM && sN == h->sNs && h->demoted_scaling == h->scaling &&
-        (!naive || h->demoted_alpha == h->alpha))
-        return GADI_OK;
     const int64_t cnt = h->n * (int64_t)h->W;
-    const double scM = std::ldexp(1.0, -sM), scN = std::ldexp(1.0, -sN);
     if (naive) {
-        // alpha rounded into the stored FP16 diagonals of H and S, nothing scaled
-        // S^T = aI + N^T keeps +alpha on its diagonal, so N^T gets its own
-        // FP16 array here even when N is skew-symmetric
-        if (!h->nt16 && dalloc(&h->nt16, cnt) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(h, GADI_ERR_OUT_OF_MEMORY, "no memory for the unscaled S^T values");
-        }
-        k_demote_diag<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->em, h->m16,
-                                                                      h->alpha, 1.0);
-        k_demote_diag<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->en, h->n16,
-                                                                      h->alpha, 1.0);
-        if (h->ent)
-            k_demote_diag<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->ent, h->nt16,
-                                                                          h->alpha, 1.0);
-        else
-            k_demote_diag<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->en, h->nt16,
-                                                                          h->alpha, -1.0);
+        k_demote_diag<TD><<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->em, m, h->alpha, 1.0);
+        k_demote_diag<TD><<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->en, nv, h->alpha, 1.0);
+        // S^T = aI + N^T keeps +alpha on its diagonal
+        k_demote_diag<TD><<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->W, h->ecol, h->ent ? h->ent : h->en,
+                                                                          nt, h->alpha, h->ent ? 1.0 : -1.0);
         if (h->HD64) {
-            k_demote_diag<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, 0, nullptr, h->HD64, h->HD16,
-                                                                           h->alpha, 1.0);
+            k_demote_diag<TD><<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, 0, nullptr, h->HD64, hd,
+                                                                               h->alpha, 1.0);
             for (int d = 0; d < h->sdim; ++d)
-                k_demote<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HK64[d], h->HK16[d], 1.0);
+                k_demote<TD><<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HK64[d], hk[d], 1.0);
         }
-    } else {
-        k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->em, h->m16, scM);
-        k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->en, h->n16, scN);
-        if (h->ent) k_demote<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->ent, h->nt16, scN);
-        if (h->HD64) {
-            k_demote<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HD64, h->HD16, scM);
-            for (int d = 0; d < h->sdim; ++d)
-                k_demote<<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HK64[d], h->HK16[d], scM);
-        }
+        return;
     }
-    CK(cudaGetLastError());
-    // entries that flush to zero or overflow in FP16 even after scaling
+    k_demote<TD><<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->em, m, scM);
+    k_demote<TD><<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->en, nv, scN);
+    if (h->ent) k_demote<TD><<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->ent, nt, scN);
+    if (h->HD64) {
+        k_demote<TD><<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HD64, hd, scM);
+        for (int d = 0; d < h->sdim; ++d)
+            k_demote<TD><<<grid_for(h->n), kSetupThreads, 0, h->stream>>>(h->n, h->HK64[d], hk[d], scM);
+    }
+}
+
+// entries that flush to zero or overflow in the inner precision after scaling
+template <class TD>
+gadi_status count_lost(gadi_solver *h, const TD *m, const TD *nv, const char *name)
+{
+    const int64_t cnt = h->n * (int64_t)h->W;
     int *lost = (int *)h->scratch;
     CK(cudaMemsetAsync(lost, 0, sizeof(int), h->stream));
-    k_count_range<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->em, h->m16, lost);
-    k_count_range<<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->en, h->n16, lost);
+    k_count_range<TD><<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->em, m, lost);
+    k_count_range<TD><<<grid_for(cnt), kSetupThreads, 0, h->stream>>>(cnt, h->en, nv, lost);
     int nlost = 0;
     CK(cudaMemcpyAsync(&nlost, lost, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    if (nlost)
-        return fail(h, GADI_ERR_RANGE, "%d matrix entries are out of FP16 range after scaling", nlost);
+    if (nlost) return fail(h, GADI_ERR_RANGE, "%d matrix entries are out of %s range after scaling", nlost, name);
+    return GADI_OK;
+}
+
+// Demote the inner operators for the current alpha and inner precision:
+// FP16 and bfloat16 with the power-of-two scaling (or FP16 unscaled), FP32
+// unscaled; FP64 needs nothing.
+gadi_status prepare_inner(gadi_solver *h)
+{
+    if (h->u_r == GADI_F64) {
+        h->sM = h->sNs = 0;
+        return GADI_OK;
+    }
+    const bool naive = h->scaling == 0 && h->u_r == GADI_F16;
+    const bool scaled = h->u_r != GADI_F32 && !naive;
+    int sM = scaled ? half_scale_exponent(h->mnorm, h->alpha) : 0;
+    int sN = scaled ? half_scale_exponent(h->nnorm, h->alpha) : 0;
+    if (h->demoted && h->demoted_ur == h->u_r && sM == h->sM && sN == h->sNs &&
+        h->demoted_scaling == h->scaling && (!naive || h->demoted_alpha == h->alpha))
+        return GADI_OK;
+    h->demoted = false;
+    const int64_t cnt = h->n * (int64_t)h->W;
+    const double scM = std::ldexp(1.0, -sM), scN = std::ldexp(1.0, -sN);
+    const bool own_nt = h->ent || naive;     // S^T needs its own array
+    gadi_status st = GADI_OK;
+    if (h->u_r == GADI_F32) {
+        bool ok = (h->m32 || !dalloc(&h->m32, cnt)) && (h->n32 || !dalloc(&h->n32, cnt)) &&
+                  (!own_nt || h->nt32 || !dalloc(&h->nt32, cnt));
+        if (ok && h->HD64) {
+            ok = h->HD32 || !dalloc(&h->HD32, h->n);
+            for (int d = 0; d < h->sdim && ok; ++d) ok = h->HK32[d] || !dalloc(&h->HK32[d], h->n);
+        }
+        if (!ok) {
+            cudaGetLastError();
+            return fail(h, GADI_ERR_OUT_OF_MEMORY, "no memory for the FP32 inner values");
+        }
+        demote_all<float>(h, h->m32, h->n32, h->nt32, h->HD32, h->HK32, false, scM, scN);
+        CK(cudaGetLastError());
+    } else {
+        if (own_nt && !h->nt16 && dalloc(&h->nt16, cnt) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, GADI_ERR_OUT_OF_MEMORY, "no memory for the S^T values");
+        }
+        if (h->u_r == GADI_F16) {
+            demote_all<__half>(h, h->m16, h->n16, h->nt16, h->HD16, h->HK16, naive, scM, scN);
+            CK(cudaGetLastError());
+            st = count_lost<__half>(h, h->m16, h->n16, "FP16");
+        } else {
+            auto bf = [](__half *p) { return reinterpret_cast<__nv_bfloat16 *>(p); };
+            __nv_bfloat16 *hk[3] = {bf(h->HK16[0]), bf(h->HK16[1]), bf(h->HK16[2])};
+            demote_all<__nv_bfloat16>(h, bf(h->m16), bf(h->n16), bf(h->nt16), bf(h->HD16), hk, false, scM, scN);
+            CK(cudaGetLastError());
+            st = count_lost<__nv_bfloat16>(h, bf(h->m16), bf(h->n16), "bfloat16");
+        }
+    }
+    if (st != GADI_OK) return st;
     h->sM = sM;
     h->sNs = sN;
     h->demoted = true;
+    h->demoted_ur = h->u_r;
     h->demoted_alpha = h->alpha;
     h->demoted_scaling = h->scaling;
     return GADI_OK;
@@ -475,16 +523,20 @@ EllOp<T> make_ell(const gadi_solver *h)
     op.W = h->W;
     op.col = h->ecol;
     op.a64 = h->ea;
-    if constexpr (std::is_same<T, __half>::value) {
-        op.m = h->m16;
-        op.nv = h->n16;
-        op.nt = (h->ent || h->scaling == 0) ? h->nt16 : nullptr;
-    } else {
+    const bool naive = h->scaling == 0 && std::is_same<T, __half>::value;
+    if constexpr (std::is_same<T, double>::value) {
         op.m = h->em;
         op.nv = h->en;
         op.nt = h->ent;
+    } else if constexpr (std::is_same<T, float>::value) {
+        op.m = h->m32;
+        op.nv = h->n32;
+        op.nt = h->ent ? h->nt32 : nullptr;
+    } else {
+        op.m = reinterpret_cast<const T *>(h->m16);
+        op.nv = reinterpret_cast<const T *>(h->n16);
+        op.nt = (h->ent || naive) ? reinterpret_cast<const T *>(h->nt16) : nullptr;
     }
-    const bool naive = h->scaling == 0 && std::is_same<T, __half>::value;
     op.sigH = naive ? Acc(0) : (Acc)std::ldexp(h->alpha, -h->sM);
     op.sigS = naive ? Acc(0) : (Acc)std::ldexp(h->alpha, -h->sNs);
     return op;
@@ -493,6 +545,16 @@ EllOp<T> make_ell(const gadi_solver *h)
 float half_round(double v)
 {
     return __half2float(__double2half(v));
+}
+
+// v rounded once to the inner storage type T (as an arithmetic value)
+template <class T>
+typename Prec<T>::Acc round_to(double v)
+{
+    if constexpr (std::is_same<T, __half>::value) return half_round(v);
+    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __bfloat162float(__double2bfloat16(v));
+    else if constexpr (std::is_same<T, float>::value) return (float)v;
+    else return v;
 }
 
 template <class T, int DIM, int R>
@@ -526,17 +588,24 @@ StencilOp<T, DIM, R> make_stencil(const gadi_solver *h)
             op.sigS = Acc(0);
             return op;
         }
-        op.h_diag = half_round(h->a_diag * scM);
-        op.h_off = half_round(h->m_off * scM);
-        op.s_c = half_round(h->n_up * scN);
-        op.HD = h->HD16;
-        for (int d = 0; d < 3; ++d) op.HK[d] = h->HK16[d];
-    } else {
+    }
+    if constexpr (std::is_same<T, double>::value) {
         op.h_diag = h->a_diag;
         op.h_off = h->m_off;
         op.s_c = h->n_up;
         op.HD = h->HD64;
         for (int d = 0; d < 3; ++d) op.HK[d] = h->HK64[d];
+    } else {
+        op.h_diag = round_to<T>(h->a_diag * scM);
+        op.h_off = round_to<T>(h->m_off * scM);
+        op.s_c = round_to<T>(h->n_up * scN);
+        if constexpr (std::is_same<T, float>::value) {
+            op.HD = h->HD32;
+            for (int d = 0; d < 3; ++d) op.HK[d] = h->HK32[d];
+        } else {
+            op.HD = reinterpret_cast<const T *>(h->HD16);
+            for (int d = 0; d < 3; ++d) op.HK[d] = reinterpret_cast<const T *>(h->HK16[d]);
+        }
     }
     op.sigH = (Acc)std::ldexp(h->alpha, -h->sM);
     op.sigS = (Acc)std::ldexp(h->alpha, -h->sNs);
@@ -601,11 +670,11 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     a.anorm = h->anorm;
     a.bnorm = bnorm;
     a.tol = tol;
-    a.eps = h->eps > 0 ? h->eps : (h->u_r == GADI_F16 ? 1e-2 : 1e-10);
+    a.eps = h->eps > 0 ? h->eps : (h->u_r == GADI_F64 ? 1e-10 : 1e-2);
     a.pfac = (2.0 - h->omega) * h->alpha;
     a.sM = h->sM;
     a.sN = h->sNs;
-    a.half = h->u_r == GADI_F16 ? 1 : 0;
+    a.half = h->u_r != GADI_F64 ? 1 : 0;     // r and z scaled by powers of two below FP64
     a.naive = (h->u_r == GADI_F16 && h->scaling == 0) ? 1 : 0;
     a.stop_kind = h->stop;
     a.max_inner = h->max_inner;
@@ -710,8 +779,12 @@ gadi_status dispatch_op(const gadi_solver *h, Fn &&fn)
 template <class Fn>
 gadi_status dispatch(const gadi_solver *h, Fn &&fn)
 {
-    if (h->u_r == GADI_F16) return dispatch_op<__half>(h, fn);
-    return dispatch_op<double>(h, fn);
+    switch (h->u_r) {
+    case GADI_F16: return dispatch_op<__half>(h, fn);
+    case GADI_BF16: return dispatch_op<__nv_bfloat16>(h, fn);
+    case GADI_F32: return dispatch_op<float>(h, fn);
+    default: return dispatch_op<double>(h, fn);
+    }
 }
 
 }  // namespace
@@ -922,8 +995,8 @@ gadi_status gadi_set_params(gadi_solver *h, double alpha, double omega, gadi_pre
     auto valid = [](int p) { return p >= GADI_F64 && p <= GADI_BF16; };
     if (!valid(u_r) || !valid(u) || !valid(u_f))
         return fail(h, GADI_ERR_INVALID_ARG, "unknown precision");
-    if (u != GADI_F64 || u_f != GADI_F64 || (u_r != GADI_F64 && u_r != GADI_F16))
-        return fail(h, GADI_ERR_UNSUPPORTED, "supported precision triples: u = u_f = F64, u_r = F16 or F64");
+    if (u != GADI_F64 || u_f != GADI_F64)
+        return fail(h, GADI_ERR_UNSUPPORTED, "supported precision triples: u = u_f = F64, any u_r");
     if (u_r != h->u_r) h->demoted = false;
     h->alpha = alpha;
     h->omega = omega;

@@ -3,6 +3,7 @@
 // all-block reductions.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "gadi_bits.cuh"
@@ -123,6 +124,83 @@ template <> struct Prec<__half> {
 #pragma unroll
             for (int k = 0; k < K; k += 2) {
                 const float2 f = __half22float2(__float22half2_rn(make_float2(v[k], v[k + 1])));
+                v[k] = f.x;
+                v[k + 1] = f.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = rnd(v[k]);
+        }
+    }
+};
+
+// FP32 storage and arithmetic (u_r = single): no rounding between steps
+template <> struct Prec<float> {
+    using Acc = float;
+    static __device__ __forceinline__ float ld(float v) { return v; }
+    static __device__ __forceinline__ float st(float v) { return v; }
+    static __device__ __forceinline__ float rnd(float v) { return v; }
+    static __device__ __forceinline__ float from64(double v) { return __double2float_rn(v); }
+    static __device__ __forceinline__ double to64(float v) { return double_of_float(v); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float madd(float c, float a, float b) { return __fmaf_rn(a, b, c); }
+    template <int K>
+    static __device__ __forceinline__ void madd_s(float (&o)[K], const float (&c)[K], float a, const float (&b)[K])
+    {
+        Prec<__half>::madd_s(o, c, a, b);
+    }
+    template <int K>
+    static __device__ __forceinline__ void madd_v(float (&o)[K], const float (&c)[K], const float (&a)[K],
+                                                  const float (&b)[K])
+    {
+        Prec<__half>::madd_v(o, c, a, b);
+    }
+    template <int K>
+    static __device__ __forceinline__ void mul_s(float (&o)[K], float a, const float (&b)[K])
+    {
+        Prec<__half>::mul_s(o, a, b);
+    }
+    template <int K>
+    static __device__ __forceinline__ void rndv(float (&)[K]) {}
+};
+
+// BF16 storage with FP32 arithmetic (a precision variant of u_r)
+template <> struct Prec<__nv_bfloat16> {
+    using Acc = float;
+    static __device__ __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float rnd(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+    static __device__ __forceinline__ __nv_bfloat16 from64(double v) { return __double2bfloat16(v); }
+    static __device__ __forceinline__ double to64(float v) { return double_of_float(v); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float madd(float c, float a, float b) { return __fmaf_rn(a, b, c); }
+    template <int K>
+    static __device__ __forceinline__ void madd_s(float (&o)[K], const float (&c)[K], float a, const float (&b)[K])
+    {
+        Prec<__half>::madd_s(o, c, a, b);
+    }
+    template <int K>
+    static __device__ __forceinline__ void madd_v(float (&o)[K], const float (&c)[K], const float (&a)[K],
+                                                  const float (&b)[K])
+    {
+        Prec<__half>::madd_v(o, c, a, b);
+    }
+    template <int K>
+    static __device__ __forceinline__ void mul_s(float (&o)[K], float a, const float (&b)[K])
+    {
+        Prec<__half>::mul_s(o, a, b);
+    }
+    template <int K>
+    static __device__ __forceinline__ void rndv(float (&v)[K])
+    {
+        if constexpr (K % 2 == 0) {
+#pragma unroll
+            for (int k = 0; k < K; k += 2) {
+                const float2 f = __bfloat1622float2(__float22bfloat162_rn(make_float2(v[k], v[k + 1])));
                 v[k] = f.x;
                 v[k + 1] = f.y;
             }

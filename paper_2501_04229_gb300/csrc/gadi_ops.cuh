@@ -77,6 +77,49 @@ __device__ __forceinline__ void stv(__half *p, int64_t j0, const float (&v)[K])
 }
 
 template <int K>
+__device__ __forceinline__ void ldv(const __nv_bfloat16 *p, int64_t j0, float (&o)[K])
+{
+    static_assert(K == 4 || K == 8, "chunk width");
+    if constexpr (K == 8) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(p + j0);
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __bfloat1622float2(h[k]);
+            o[2 * k] = f.x;
+            o[2 * k + 1] = f.y;
+        }
+    } else {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p + j0);
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float2 f = __bfloat1622float2(h[k]);
+            o[2 * k] = f.x;
+            o[2 * k + 1] = f.y;
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void stv(__nv_bfloat16 *p, int64_t j0, const float (&v)[K])
+{
+    if constexpr (K == 8) {
+        uint4 u;
+        __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[k] = __float22bfloat162_rn(make_float2(v[2 * k], v[2 * k + 1]));
+        *reinterpret_cast<uint4 *>(p + j0) = u;
+    } else {
+        uint2 u;
+        __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) h[k] = __float22bfloat162_rn(make_float2(v[2 * k], v[2 * k + 1]));
+        *reinterpret_cast<uint2 *>(p + j0) = u;
+    }
+}
+
+template <int K>
 __device__ __forceinline__ void ldv(const float *p, int64_t j0, float (&o)[K])
 {
     const float4 *q = reinterpret_cast<const float4 *>(p + j0);

@@ -41,7 +41,8 @@ struct SolveArgs {
     float *r32;                  // n floats: round-to-odd copy of r (FP16 inner path)
     T *v[9];                     // inner work vectors, n elements each
     double anorm, bnorm, tol, eps, pfac;
-    int sM, sN, half, stop_kind;
+    int sM, sN, stop_kind;
+    int half;                    // inner precision below FP64: r and z scaled by powers of two
     int naive;                   // unscaled FP16 mode: no 2^-e, 2^-ez; (2-w) a applied to z in FP16
     int max_inner, max_outer;
     Ctl *ctl;

@@ -356,9 +356,13 @@ def test_invalid_arguments_rejected():
             with pytest.raises(G.GadiError) as e:
                 G.gadi_set_params(h, a, w)
             assert e.value.status == G.GADI_ERR_INVALID_ARG
+        for kw in (dict(u=G.GADI_F32), dict(u_f=G.GADI_F16)):
+            with pytest.raises(G.GadiError) as e:
+                G.gadi_set_params(h, 1.0, 1.0, **kw)
+            assert e.value.status == G.GADI_ERR_UNSUPPORTED
         with pytest.raises(G.GadiError) as e:
-            G.gadi_set_params(h, 1.0, 1.0, u_r=G.GADI_F32)
-        assert e.value.status == G.GADI_ERR_UNSUPPORTED
+            G.gadi_set_params(h, 1.0, 1.0, u_r=7)
+        assert e.value.status == G.GADI_ERR_INVALID_ARG
         b = _dev(p.b)
         x = torch.full((p.n,), 7.0, dtype=torch.float64, device="cuda")
         with pytest.raises(G.GadiError):
@@ -576,5 +580,96 @@ def test_naive_fp16_loose_tolerance_matches_oracle():
         assert abs(info["outer_iters"] - oinfo["outer_iters"]) <= max(2, 0.15 * oinfo["outer_iters"])
         with pytest.raises(G.GadiError):
             G.gadi_set_scaling(h, 2)
+    finally:
+        G.gadi_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# other inner precisions: FP32 and bfloat16 storage (precision variants)
+# ---------------------------------------------------------------------------
+
+def _bf16_vector(n, seed):
+    bits = oracle.to_bf16_bits(P.random_vector(n, seed))
+    return bits, (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def _lp_tensor(x, u_r, bits=None):
+    if u_r == G.GADI_BF16:
+        return torch.from_numpy(bits.view(np.int16).copy()).cuda().view(torch.bfloat16)
+    return _dev(x, torch.float32)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("kernel", [G.GADI_KERNEL_SPARSE, G.GADI_KERNEL_STENCIL])
+@pytest.mark.parametrize("u_r,prec", [(G.GADI_F32, oracle.PREC_SINGLE), (G.GADI_BF16, oracle.PREC_BF16)])
+def test_apply_other_precisions_bit_exact(name, kernel, u_r, prec):
+    p = PROBLEMS[name]()
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 0.37, 1.0, u_r=u_r)
+        G.gadi_set_kernel(h, kernel)
+        for which in (G.OP_H, G.OP_S, G.OP_ST):
+            if u_r == G.GADI_BF16:
+                bits, x = _bf16_vector(p.n, 70 + which)
+            else:
+                bits, x = None, P.random_vector(p.n, 70 + which).astype(np.float32).astype(np.float64)
+            want, sM, sN = oracle.lp_apply(p.A, 0.37, which, prec, x)
+            xd = _lp_tensor(x, u_r, bits)
+            yd = torch.empty_like(xd)
+            G.gadi_apply(h, which, xd, yd)
+            torch.cuda.synchronize()
+            got = yd.double().cpu().numpy()
+            if kernel == G.GADI_KERNEL_STENCIL and p.faces is not None and u_r == G.GADI_F32 \
+                    and which in (G.OP_S, G.OP_ST):
+                # the face stencil applies N as the constant c = beta h / 2 (see the FP64 case)
+                assert np.allclose(got, want, rtol=1e-6, atol=1e-7 * np.abs(want).max())
+            else:
+                assert np.array_equal(got, want), (which, np.abs(got - want).max())
+        assert G.gadi_get_scales(h) == (sM, sN)
+    finally:
+        G.gadi_destroy(h)
+
+
+@pytest.mark.parametrize("rows", [1, 4, 8])
+@pytest.mark.parametrize("u_r,prec", [(G.GADI_F32, oracle.PREC_SINGLE), (G.GADI_BF16, oracle.PREC_BF16)])
+def test_apply_other_precisions_item_rows(rows, u_r, prec):
+    p = ROWS_PROBLEMS["3d_16_b40"]()
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 2.0, 1.0, u_r=u_r)
+        G.gadi_set_kernel(h, G.GADI_KERNEL_STENCIL)
+        G.gadi_set_item_rows(h, rows)
+        for which in (G.OP_H, G.OP_S, G.OP_ST):
+            if u_r == G.GADI_BF16:
+                bits, x = _bf16_vector(p.n, 80 + which)
+            else:
+                bits, x = None, P.random_vector(p.n, 80 + which).astype(np.float32).astype(np.float64)
+            want, _, _ = oracle.lp_apply(p.A, 2.0, which, prec, x)
+            xd = _lp_tensor(x, u_r, bits)
+            yd = torch.empty_like(xd)
+            G.gadi_apply(h, which, xd, yd)
+            torch.cuda.synchronize()
+            assert np.array_equal(yd.double().cpu().numpy(), want), (rows, which)
+    finally:
+        G.gadi_destroy(h)
+
+
+@pytest.mark.parametrize("u_r,prec", [(G.GADI_F32, oracle.PREC_SINGLE), (G.GADI_BF16, oracle.PREC_BF16)])
+@pytest.mark.parametrize("kernel", [G.GADI_KERNEL_SPARSE, G.GADI_KERNEL_STENCIL])
+def test_other_precision_solves_match_oracle(u_r, prec, kernel):
+    p = PROBLEMS["3d_13_b100"]()
+    want, oinfo, _ = oracle.gadi_ir(p.A, p.b, 3.0, 1.0, tol=1e-13, eps_inner=1e-2, prec=prec, max_outer=5000)
+    assert oinfo["status"] == oracle.OK
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 3.0, 1.0, u_r=u_r)
+        G.gadi_set_inner(h, 1e-2, 200, 5000)
+        G.gadi_set_kernel(h, kernel)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK, G.last_error(h)
+        assert oracle.backward_error(p.A, p.b, x) <= 1e-13
+        assert np.linalg.norm(x - want) <= 1e-9 * np.linalg.norm(want)
+        assert abs(info["outer_iters"] - oinfo["outer_iters"]) <= max(2, 0.15 * oinfo["outer_iters"])
+        assert (info["scale_exp_M"], info["scale_exp_N"]) == (oinfo["scale_exp_M"], oinfo["scale_exp_N"])
     finally:
         G.gadi_destroy(h)

@@ -220,13 +220,14 @@ def test_manufactured_solution_config_2d(oracle_lib):
     assert np.linalg.norm(x - 1.0) <= rnorm / lam_min * (1 + 1e-6) + 1e-14
 
 
-def test_fp16_inner_reaches_fp64_floor(oracle_lib):
+@pytest.mark.parametrize("prec", ["PREC_HALF", "PREC_BF16", "PREC_SINGLE"])
+def test_low_precision_inner_reaches_fp64_floor(oracle_lib, prec):
     """Cor. 1: the limiting accuracy depends on u and u_f only. With scaling,
-    FP16 inner solves reach the same eta as FP64 inner solves, in the same
-    number of outer steps up to a few."""
+    FP16 (and bfloat16, FP32) inner solves reach the same eta as FP64 inner
+    solves, in the same number of outer steps up to a few."""
     p = P.workload("convdiff2d_32_b10")
     x16, i16, _ = oracle_lib.gadi_ir(p.A, p.b, 0.5, 1.0, tol=1e-13, eps_inner=1e-2,
-                                     prec=oracle_lib.PREC_HALF)
+                                     prec=getattr(oracle_lib, prec))
     x64, i64, _ = oracle_lib.gadi_ir(p.A, p.b, 0.5, 1.0, tol=1e-13, eps_inner=1e-2,
                                      prec=oracle_lib.PREC_DOUBLE)
     assert i16["status"] == oracle_lib.OK and i64["status"] == oracle_lib.OK
@@ -348,6 +349,51 @@ def test_fp16_rounding_is_ieee_rne(oracle_lib):
     assert np.array_equal(got, want)
     with np.errstate(over="ignore"):
         assert np.array_equal(got, x.astype(np.float16).view(np.uint16))
+
+
+def _bf16_bits_ref(x: float) -> int:
+    """bfloat16 encoding of x (8 significant bits, exponent range of IEEE
+    binary32: normal down to 2^-126, subnormal steps 2^-133), round to
+    nearest, ties to even, with exact rational arithmetic."""
+    if math.isnan(x):
+        return 0x7FC0
+    sign = 0x8000 if math.copysign(1.0, x) < 0 else 0
+    a = abs(x)
+    if a == 0.0:
+        return sign
+    if math.isinf(a):
+        return sign | 0x7F80
+    e = math.frexp(a)[1] - 1
+    e = max(e, -126)
+    q = Fraction(2) ** (e - 7)
+    m = Fraction(a) / q
+    mi = math.floor(m)
+    rem = m - mi
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and mi % 2 == 1):
+        mi += 1
+    if mi == 256:
+        mi, e = 128, e + 1
+    if e > 127:
+        return sign | 0x7F80
+    if mi < 128:
+        return sign | mi
+    return sign | ((e + 127) << 7) | (mi - 128)
+
+
+def test_bf16_rounding_is_rne_with_one_rounding(oracle_lib):
+    """The bfloat16 inner-precision variant rounds FP64 values once to 8
+    significant bits (not through an intermediate FP32 rounding)."""
+    rng = np.random.default_rng(321)
+    vals = np.exp2(rng.uniform(-140, 130, 4000)) * rng.choice([-1.0, 1.0], 4000)
+    ties = [(k + 0.5) * 2.0 ** -7 for k in range(128, 150)]            # halfway in the normal range
+    ties += [(k + 0.5) * 2.0 ** -133 for k in range(0, 20)]            # halfway between subnormals
+    # just above a tie by less than FP32's resolution: rounding through FP32 would create the tie
+    ties += [(129 + 0.5) * 2.0 ** -7 * (1 + 2.0 ** -40), (130 + 0.5) * 2.0 ** -7 * (1 - 2.0 ** -40)]
+    special = [0.0, -0.0, 3.3895313892515355e38, 3.4e38, 1e39, 2.0 ** -134, 2.0 ** -135, 1.0 / 3.0]
+    x = np.concatenate([vals, ties, special])
+    got = oracle_lib.to_bf16_bits(x)
+    want = np.array([_bf16_bits_ref(float(v)) for v in x], dtype=np.uint16)
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
 
 
 def test_fp16_parameters_of_table1(oracle_lib):
