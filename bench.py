@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GADI comparison")
     ap.add_argument("--no-spmv", action="store_true", help="skip the operator bandwidth runs")
     ap.add_argument("--no-hbm", action="store_true", help="skip the 192^3 HBM-bound case")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the inner-precision ablation")
     ap.add_argument("--workload", default=WORKLOAD, help="system of problems.WORKLOADS to time")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0,
                     help="bound on the CPU oracle's time for cpu_baseline")
@@ -335,6 +336,34 @@ def hbm_case(G, torch, P, predictor, args, flush_l2, stream, N, beta):
     return out
 
 
+def precision_ablation(G, h, b, x, alpha, omega, flush_l2, stream, torch):
+    """The inner precision u_r varied on the same system and parameters (§4.1's
+    precision study): FP16 (scaled, the method), bfloat16 (scaled), FP32,
+    FP64, and the unscaled FP16 mode. One solve each to eta_inf <= 1e-13
+    (the unscaled mode is capped at 2000 outer steps: it stalls), L2 flushed
+    before each, CUDA-event time."""
+    out = {}
+    for name, u_r, scaling, eps in (("fp16", G.GADI_F16, 1, EPS16), ("bf16", G.GADI_BF16, 1, EPS16),
+                                    ("fp32", G.GADI_F32, 1, EPS16), ("fp64", G.GADI_F64, 1, EPS16),
+                                    ("fp16_unscaled", G.GADI_F16, 0, EPS16)):
+        G.gadi_set_params(h, alpha, omega, u_r=u_r)
+        G.gadi_set_scaling(h, scaling)
+        G.gadi_set_inner(h, eps, 500, 2000 if scaling == 0 else 100000)
+        x.zero_()
+        flush_l2()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = G.gadi_solve(h, b, x, TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"status": G.status_str(st), "time_s": e0.elapsed_time(e1) * 1e-3,
+                     "outer_iters": info["outer_iters"], "inner_iters_H": info["inner_iters_H"],
+                     "inner_iters_S": info["inner_iters_S"], "eta_inf": info["eta_inf"]}
+    G.gadi_set_scaling(h, 1)
+    return out
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_2501_04229_gb300 import build as B
@@ -440,6 +469,9 @@ def run_gpu(args, rank, world):
                                     (("stencil", G.GADI_KERNEL_STENCIL),), flush_l2, stream))
         del p192
     G.gadi_set_kernel(h, kern)
+    ablation = None
+    if not args.no_ablation:
+        ablation = precision_ablation(G, h, b, x, args.alpha, args.omega, flush_l2, stream, torch)
     configure(G.GADI_F16)
 
     # the HBM-bound case: the same method on the 192^3 system
@@ -472,7 +504,7 @@ def run_gpu(args, rank, world):
     achieved = algorithmic_bytes(n, nnz, info, args.kernel, True) / statistics.mean(kern_t) / 1e9
     return {
         "ms_per_step": ms_per_step, "value": tot / args.steps, "info": info, "eta_gpu": eta_gpu,
-        "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(), "hbm_case": hbm_res,
+        "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(), "hbm_case": hbm_res, "ablation": ablation,
         "e2e": statistics.mean(e2e), "predictor": predictor, "roofline": {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4),
@@ -580,6 +612,7 @@ def main():
         "speedup_vs_fp64_gadi": (r["fp64"]["time_s"] / r["value"]) if r["fp64"] else None,
         "spmv": r["spmv"],
         "hbm_case": r["hbm_case"],
+        "precision_ablation": r["ablation"],
     })
     print(json.dumps(line))
 
