@@ -230,12 +230,13 @@ def apply_bandwidth(G, torch, p, stencil, kernels, flush_l2, stream, reps=10):
 
 def learned_params(G, queries):
     """Training records from a batched sweep of small 3D systems of the same
-    structure (sides 8..48, 5 convection strengths, 12 alpha x 3 omega), then
+    structure (sides 8..48, 5 convection strengths, 24 alpha in [0.1, 31.6]
+    x 2 omega: a fine alpha grid keeps the targets from being quantised), then
     the MLP (trained on the GPU) and the GPR; their (alpha, omega) for each
     (n, beta) of queries (the first one is reported at the top level)."""
     from paper_2501_04229_gb300 import sweep as SW
     inst = [(3, N, b) for N in (8, 16, 24, 32, 40, 48) for b in (2.0, 10.0, 40.0, 100.0, 300.0)]
-    cands = SW.candidates(n_alpha=12, omegas=(0.0, 0.5, 1.0), lo=-1.0, hi=1.5)
+    cands = SW.candidates(n_alpha=24, omegas=(0.0, 0.5), lo=-1.0, hi=1.5)
     t0 = time.perf_counter()
     recs = SW.run(inst, cands=cands, eps_inner=EPS16, max_outer=4000)
     t_sweep = time.perf_counter() - t0
