@@ -90,6 +90,9 @@ def _load():
                                   p_f64, p_f64, p_i32, p_i32]),
         "or_to_half_bits": (None, [i64, p_f64, p_u16]),
         "or_to_bf16_bits": (None, [i64, p_f64, p_u16]),
+        "or_sylv_norm_inf": (f64, [i64, i64, p_f64, p_f64, p_f64, p_f64, p_f64, p_f64]),
+        "or_sylv_gadi_ab": (C.c_int, [i64, i64, p_f64, p_f64, p_f64, p_f64, p_f64, p_f64, p_f64, p_f64,
+                                  f64, f64, C.c_int32, f64, C.c_int32, C.POINTER(Info), p_f64]),
         "or_wtime": (f64, []),
     }
     for name, (res, args) in sig.items():
@@ -239,6 +242,48 @@ def gadi_ir(A, b, alpha, omega, tol=1e-13, eps_inner=1e-2, max_inner=200, max_ou
                     max_outer, stop, prec, m_user=m_user)
     return _run("or_gadi_ir", A, b, x0, alpha, omega, tol, eps_inner, max_inner, max_outer, stop,
                 prec)
+
+
+def sylvester_matrices(n, r):
+    """The tridiagonal test matrix of §4.3, A = B = M + 2 r N + 100/(n+1)^2 I
+    with M = tridiag(-1, 2, -1) and N = tridiag(0.5, 0, -0.5), as
+    (lo, dg, up) with lo[i] = T[i][i-1], up[i] = T[i][i+1]."""
+    lo = np.full(n, -1.0 + 2.0 * r * 0.5)
+    up = np.full(n, -1.0 + 2.0 * r * (-0.5))
+    dg = np.full(n, 2.0 + 100.0 / (n + 1) ** 2)
+    lo[0] = 0.0
+    up[-1] = 0.0
+    return lo, dg, up
+
+
+def tri_dense(lo, dg, up):
+    n = len(dg)
+    T = np.diag(dg).astype(np.float64)
+    T[np.arange(1, n), np.arange(n - 1)] = lo[1:]
+    T[np.arange(n - 1), np.arange(1, n)] = up[:-1]
+    return T
+
+
+def sylv_norm_inf(a, b):
+    m, n = len(a[1]), len(b[1])
+    arrs = [_f64(v) for v in (*a, *b)]
+    return _load().or_sylv_norm_inf(m, n, *[_p(v, C.c_double) for v in arrs])
+
+
+def sylv_gadi_ab(a, b, Cm, alpha, omega, prec=PREC_HALF, tol=1e-13, max_outer=10000, x0=None):
+    """GADI-AB for A X + X B = C (see or_sylv_gadi_ab); a, b = (lo, dg, up).
+    Returns (X, info, eta history)."""
+    m, n = len(a[1]), len(b[1])
+    arrs = [_f64(v) for v in (*a, *b)]
+    Cm = np.ascontiguousarray(Cm, dtype=np.float64)
+    X = np.zeros((m, n)) if x0 is None else np.array(x0, dtype=np.float64, order="C")
+    info = Info()
+    hist = np.zeros(max_outer + 1)
+    _load().or_sylv_gadi_ab(m, n, *[_p(v, C.c_double) for v in arrs], _p(Cm, C.c_double), _p(X, C.c_double),
+                            float(alpha), float(omega), int(prec), float(tol), int(max_outer), C.byref(info),
+                            _p(hist, C.c_double))
+    d = info.as_dict()
+    return X, d, hist[:d["outer_iters"] + 1]
 
 
 def lp_apply(A, alpha, which, prec, x, m_user=None):

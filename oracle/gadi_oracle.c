@@ -891,3 +891,219 @@ double or_wtime(void)
     return 0.0;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* GADI-AB: GADI-IR (Algorithm 1) for the Sylvester equation (§4.3)    */
+/*     A X + X B = C,  A (m x m), B (n x n) tridiagonal, X, C (m x n) */
+/* The operator L(X) = A X + X B is split into X -> A X and X -> X B   */
+/* (the paper's GADI-AB: M, N of Algorithm 1 replaced by A, B). One   */
+/* outer step:                                                         */
+/*   R = C - A X - X B                         (FP64, u_f)              */
+/*   e = floor(log2 max|R|), R^ = fl_r(2^-e R)                          */
+/*   Z = H'^-1 R^,  H' = 2^-sA (aI + A)          columns of R^          */
+/*   ez = floor(log2 max|Z|), Z^ = fl_r(2^-ez Z)                        */
+/*   Y = Z^ S'^-1,  S' = 2^-sB (aI + B)          rows of Z^             */
+/*   X = X + (2-w) a 2^(e - sA + ez - sB) Y      (FP64, u)              */
+/* Readings: the residual sign follows R = C - A X - X B (the paper    */
+/* writes both A X + X B + C = 0 and this residual); the inner systems */
+/* are tridiagonal and, for a > 0 and these A, B, diagonally dominant, */
+/* so each is solved directly (Thomas: no pivoting, stable here) in    */
+/* the inner precision: factors from FP64, stored in FP32 (FP64 for    */
+/* the FP64 inner path), every stored intermediate rounded to u_r.     */
+/* Matrices: lo[i] = T[i][i-1] (lo[0] unused), dg[i] = T[i][i],        */
+/* up[i] = T[i][i+1] (up[m-1] unused). X, C row-major.                 */
+/* ------------------------------------------------------------------ */
+
+/* (|sigma| + max row sum of |T|) 2^-s in (1, 2] */
+static int tri_scale_exponent(int64_t m, const double *lo, const double *dg, const double *up, double sigma)
+{
+    double nrm = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double s = fabs(dg[i]);
+        if (i > 0) s += fabs(lo[i]);
+        if (i < m - 1) s += fabs(up[i]);
+        if (s > nrm) nrm = s;
+    }
+    nrm += fabs(sigma);
+    if (!(nrm > 0.0) || !isfinite(nrm)) return 0;
+    int e;
+    double mm = frexp(nrm, &e);
+    return ((mm == 0.5) ? e - 1 : e) - 1;
+}
+
+/* Thomas factors of T = 2^-s (sigma I + tridiag(lo, dg, up)):
+ * w_0 = t_00, w_i = t_ii - t_i,i-1 c_(i-1) (one fused multiply-add),
+ * c_i = t_i,i+1 / w_i; returns ls = scaled lo, c, iw = 1 / w. */
+static void tri_factor(int64_t m, const double *lo, const double *dg, const double *up, double sigma, int s,
+                       double *ls, double *c, double *iw)
+{
+    double w = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double d = ldexp(sigma + dg[i], -s);
+        ls[i] = i > 0 ? ldexp(lo[i], -s) : 0.0;
+        w = i > 0 ? fma(-ls[i], c[i - 1], d) : d;
+        iw[i] = 1.0 / w;
+        c[i] = i < m - 1 ? ldexp(up[i], -s) / w : 0.0;
+    }
+}
+
+/* Solve T v = rhs in place along a strided line, low precision: forward
+ * y_i = fl(fl32(fmaf(-l_i, y_(i-1), v_i)) * iw_i), back
+ * z_i = fl(fmaf(-c_i, z_(i+1), y_i)); fl = rounding to the storage type. */
+static void tri_solve32(int64_t m, int64_t stride, const float *ls, const float *c, const float *iw, float *v, int rt)
+{
+    float y = rnd_store(v[0] * iw[0], rt);
+    v[0] = y;
+    for (int64_t i = 1; i < m; ++i) {
+        y = rnd_store(fmaf(-ls[i], y, v[i * stride]) * iw[i], rt);
+        v[i * stride] = y;
+    }
+    float z = y;
+    for (int64_t i = m - 2; i >= 0; --i) {
+        z = rnd_store(fmaf(-c[i], z, v[i * stride]), rt);
+        v[i * stride] = z;
+    }
+}
+
+static void tri_solve64(int64_t m, int64_t stride, const double *ls, const double *c, const double *iw, double *v)
+{
+    double y = v[0] * iw[0];
+    v[0] = y;
+    for (int64_t i = 1; i < m; ++i) {
+        y = fma(-ls[i], y, v[i * stride]) * iw[i];
+        v[i * stride] = y;
+    }
+    double z = y;
+    for (int64_t i = m - 2; i >= 0; --i) {
+        z = fma(-c[i], z, v[i * stride]);
+        v[i * stride] = z;
+    }
+}
+
+/* R = C - A X - X B, each entry one chain of fused multiply-adds in the
+ * order A's (i-1, i, i+1), then B's (j-1, j, j+1) */
+static void sylv_residual(int64_t m, int64_t n, const double *al, const double *ad, const double *au,
+                          const double *bl, const double *bd, const double *bu, const double *C,
+                          const double *X, double *R)
+{
+    #pragma omp parallel for schedule(static) if (m * n > OR_PAR_MIN)
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            const double *x = X + i * n + j;
+            double r = C[i * n + j];
+            if (i > 0) r = fma(-al[i], x[-n], r);
+            r = fma(-ad[i], x[0], r);
+            if (i < m - 1) r = fma(-au[i], x[n], r);
+            if (j > 0) r = fma(-bu[j - 1], x[-1], r);     /* B[j-1][j] */
+            r = fma(-bd[j], x[0], r);
+            if (j < n - 1) r = fma(-bl[j + 1], x[1], r);  /* B[j+1][j] */
+            R[i * n + j] = r;
+        }
+}
+
+/* ||L||_inf of X -> A X + X B on vec(X): the largest row sum of
+ * I (x) A + B^T (x) I */
+double or_sylv_norm_inf(int64_t m, int64_t n, const double *al, const double *ad, const double *au,
+                        const double *bl, const double *bd, const double *bu)
+{
+    double best = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double sa = (i > 0 ? fabs(al[i]) : 0.0) + (i < m - 1 ? fabs(au[i]) : 0.0);
+        for (int64_t j = 0; j < n; ++j) {
+            double sb = (j > 0 ? fabs(bu[j - 1]) : 0.0) + (j < n - 1 ? fabs(bl[j + 1]) : 0.0);
+            double s = sa + sb + fabs(ad[i] + bd[j]);
+            if (s > best) best = s;
+        }
+    }
+    return best;
+}
+
+/* GADI-AB to eta = max|R| / (||L||_inf max|X| + max|C|) <= tol. prec:
+ * OR_PREC_DOUBLE, _SINGLE, _HALF or _BF16 (the FP16 and bfloat16 inner
+ * paths scale H, S, R and Z by powers of two as the vector method does).
+ * X holds x0 on entry. */
+int or_sylv_gadi_ab(int64_t m, int64_t n, const double *al, const double *ad, const double *au,
+                    const double *bl, const double *bd, const double *bu, const double *C, double *X,
+                    double alpha, double omega, int prec, double tol, int32_t max_outer, or_info *info,
+                    double *eta_hist)
+{
+    memset(info, 0, sizeof *info);
+    if (m < 1 || n < 1 || !(alpha > 0.0) || !(omega >= 0.0 && omega < 2.0) || max_outer < 0 ||
+        (prec != OR_PREC_DOUBLE && prec != OR_PREC_SINGLE && prec != OR_PREC_HALF && prec != OR_PREC_BF16)) {
+        info->status = OR_INVALID;
+        return OR_INVALID;
+    }
+    const int64_t mn = m * n;
+    const int low = prec != OR_PREC_DOUBLE;
+    const int rt = prec == OR_PREC_HALF ? RT_F16 : (prec == OR_PREC_BF16 ? RT_BF16 : RT_F32);
+    const int scaled = prec == OR_PREC_HALF || prec == OR_PREC_BF16;
+    /* the row solves use S'^T: sub-diagonal B[j-1][j] = bu[j-1], super B[j+1][j] = bl[j+1] */
+    double *btl = (double *)calloc((size_t)n, sizeof(double)), *btu = (double *)calloc((size_t)n, sizeof(double));
+    for (int64_t j = 0; j < n; ++j) {
+        btl[j] = j > 0 ? bu[j - 1] : 0.0;
+        btu[j] = j < n - 1 ? bl[j + 1] : 0.0;
+    }
+    const int sA = scaled ? tri_scale_exponent(m, al, ad, au, alpha) : 0;
+    const int sB = scaled ? tri_scale_exponent(n, btl, bd, btu, alpha) : 0;
+    info->scale_exp_M = sA;
+    info->scale_exp_N = sB;
+    double *la = (double *)malloc((size_t)m * sizeof(double)), *ca = (double *)malloc((size_t)m * sizeof(double));
+    double *iwa = (double *)malloc((size_t)m * sizeof(double));
+    double *lb = (double *)malloc((size_t)n * sizeof(double)), *cb = (double *)malloc((size_t)n * sizeof(double));
+    double *iwb = (double *)malloc((size_t)n * sizeof(double));
+    tri_factor(m, al, ad, au, alpha, sA, la, ca, iwa);
+    tri_factor(n, btl, bd, btu, alpha, sB, lb, cb, iwb);
+    float *laf = (float *)malloc((size_t)m * sizeof(float)), *caf = (float *)malloc((size_t)m * sizeof(float));
+    float *iwaf = (float *)malloc((size_t)m * sizeof(float));
+    float *lbf = (float *)malloc((size_t)n * sizeof(float)), *cbf = (float *)malloc((size_t)n * sizeof(float));
+    float *iwbf = (float *)malloc((size_t)n * sizeof(float));
+    for (int64_t i = 0; i < m; ++i) { laf[i] = (float)la[i]; caf[i] = (float)ca[i]; iwaf[i] = (float)iwa[i]; }
+    for (int64_t j = 0; j < n; ++j) { lbf[j] = (float)lb[j]; cbf[j] = (float)cb[j]; iwbf[j] = (float)iwb[j]; }
+
+    double *R = (double *)malloc((size_t)mn * sizeof(double));
+    float *Zf = (float *)malloc((size_t)mn * sizeof(float));
+    const double Ln = or_sylv_norm_inf(m, n, al, ad, au, bl, bd, bu);
+    double cmax = 0.0;
+    for (int64_t k = 0; k < mn; ++k) cmax = fmax(cmax, fabs(C[k]));
+    const double pfac = (2.0 - omega) * alpha;
+    int status = OR_NOT_CONVERGED, k = 0;
+    for (;;) {
+        sylv_residual(m, n, al, ad, au, bl, bd, bu, C, X, R);
+        double rmax = 0.0, xmax = 0.0;
+        for (int64_t q = 0; q < mn; ++q) {
+            rmax = fmax(rmax, fabs(R[q]));
+            xmax = fmax(xmax, fabs(X[q]));
+        }
+        if (!isfinite(rmax)) { status = OR_DIVERGED; break; }
+        double den = Ln * xmax + cmax;
+        info->eta_inf = den > 0.0 ? rmax / den : (rmax == 0.0 ? 0.0 : INFINITY);
+        if (eta_hist) eta_hist[k] = info->eta_inf;
+        if (info->eta_inf <= tol) { status = OR_OK; break; }
+        if (k >= max_outer) break;
+        double upd;
+        if (!low) {
+            for (int64_t i = 0; i < n; ++i) tri_solve64(m, n, la, ca, iwa, R + i);    /* columns */
+            for (int64_t i = 0; i < m; ++i) tri_solve64(n, 1, lb, cb, iwb, R + i * n); /* rows */
+            upd = pfac;
+            for (int64_t q = 0; q < mn; ++q) X[q] = fma(upd, R[q], X[q]);
+        } else {
+            int e = rmax > 0.0 ? ilog2_floor(rmax) : 0;
+            for (int64_t q = 0; q < mn; ++q) Zf[q] = rnd_from64(ldexp(R[q], -e), rt);
+            for (int64_t j = 0; j < n; ++j) tri_solve32(m, n, laf, caf, iwaf, Zf + j, rt);
+            float zmax = 0.0f;
+            for (int64_t q = 0; q < mn; ++q) zmax = fmaxf(zmax, fabsf(Zf[q]));
+            int ez = (zmax > 0.0f && isfinite(zmax)) ? ilog2_floor((double)zmax) : 0;
+            for (int64_t q = 0; q < mn; ++q) Zf[q] = rnd_store(ldexpf(Zf[q], -ez), rt);
+            for (int64_t i = 0; i < m; ++i) tri_solve32(n, 1, lbf, cbf, iwbf, Zf + i * n, rt);
+            upd = ldexp(pfac, e - sA + ez - sB);
+            for (int64_t q = 0; q < mn; ++q) X[q] = fma(upd, (double)Zf[q], X[q]);
+        }
+        info->spmv_count++;
+        ++k;
+    }
+    info->outer_iters = k;
+    info->status = status;
+    free(btl); free(btu); free(la); free(ca); free(iwa); free(lb); free(cb); free(iwb);
+    free(laf); free(caf); free(iwaf); free(lbf); free(cbf); free(iwbf); free(R); free(Zf);
+    return status;
+}
