@@ -349,6 +349,43 @@ GADI_API void gadi_destroy(gadi_solver *h);
 GADI_API const char *gadi_status_str(gadi_status s);
 GADI_API const char *gadi_last_error(const gadi_solver *h);
 
+/* ------------------------------------------------------------------------
+ * GADI-AB for the Sylvester equation A X + X B = C (§4.3): Algorithm 1
+ * with the operator X -> A X + X B split into X -> A X and X -> X B. A
+ * (m x m) and B (n x n) are tridiagonal: lo[i] = T[i][i-1] (lo[0]
+ * ignored), diag[i] = T[i][i], up[i] = T[i][i+1] (up[last] ignored). The
+ * residual is R = C - A X - X B in FP64; the two inner systems per outer
+ * step, (aI + A) Z = R^ column by column and Y (aI + B) = Z^ row by row,
+ * are tridiagonal and solved directly in the inner precision u_r (FP16 and
+ * bfloat16 with the power-of-two scaling of the vector method, FP32, or
+ * FP64); X is updated in FP64. Stop: eta = max|R| / (||L||_inf max|X| +
+ * max|C|) <= tol, with ||L||_inf the largest row sum of I (x) A + B^T (x) I.
+ * ------------------------------------------------------------------------ */
+typedef struct gadi_sylv gadi_sylv;
+
+/* Copies the host arrays (m >= 1, n >= 1, m n <= 2^31, finite values).
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+GADI_API gadi_status gadi_sylv_create(int64_t m, int64_t n, const double *a_lo, const double *a_diag,
+                                      const double *a_up, const double *b_lo, const double *b_diag,
+                                      const double *b_up, void *cuda_stream, gadi_sylv **out);
+
+/* alpha > 0, omega in [0, 2) (Thm 1), u_r any gadi_precision. */
+GADI_API gadi_status gadi_sylv_set_params(gadi_sylv *s, double alpha, double omega, gadi_precision u_r);
+
+/* Solve in place: C and X are device pointers to row-major m x n FP64
+ * arrays (X: in x0, out the result). Returns OK, NOT_CONVERGED (max_outer
+ * reached; X holds the last iterate), DIVERGED, INVALID_ARG or CUDA. info
+ * (may be NULL) gets outer_iters, eta_inf (also in res_rel), t_solve_s
+ * (host wall time of the solve, synchronised), scale_exp_M / _N = the
+ * exponents of A's and B's inner operators. */
+GADI_API gadi_status gadi_sylv_solve(gadi_sylv *s, const double *C, double *X, double tol, int32_t max_outer,
+                                     gadi_info *info);
+
+GADI_API const char *gadi_sylv_last_error(const gadi_sylv *s);
+
+/* Release all device memory of s. NULL is accepted. */
+GADI_API void gadi_sylv_destroy(gadi_sylv *s);
+
 #ifdef __cplusplus
 }
 #endif

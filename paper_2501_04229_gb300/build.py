@@ -19,11 +19,13 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgadi.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["gadi_api.cu", "gadi_noalloc.cu", "gadi_sweep.cu", "gadi_predict.cu"]
-HEADERS = ["gadi_solve.cuh", "gadi_ops.cuh", "gadi_device.cuh"]
+SOURCES = ["gadi_api.cu", "gadi_noalloc.cu", "gadi_sweep.cu", "gadi_predict.cu", "gadi_sylvester.cu"]
+HEADERS = ["gadi_solve.cuh", "gadi_ops.cuh", "gadi_device.cuh", "gadi_bits.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+# host code without floating-point contraction: set-up and stop-test arithmetic
+# rounds each product and sum as written, on x86 and Arm alike
 FLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
-         "-fvisibility=hidden", "-I", os.path.join(ROOT, "include")]
+         "-fvisibility=hidden", "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
 
 
 def nvcc() -> str:

@@ -125,7 +125,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
         }
         ++spmv;
         const double rinf = vR[1], rn2 = sqrt(vR[0]), xinf = vR[2];
-        const double den = a.anorm * xinf + a.bnorm;
+        const double den = __dadd_rn(__dmul_rn(a.anorm, xinf), a.bnorm);   // as written, not fused
         eta = den > 0.0 ? rinf / den : (rinf == 0.0 ? 0.0 : INFINITY);
         if (k == 0) r0 = rn2;
         res = r0 > 0.0 ? rn2 / r0 : 0.0;

@@ -31,7 +31,8 @@ EXPORTS = [
     "gadi_apply", "gadi_get_scales", "gadi_predict_params", "gadi_destroy", "gadi_status_str",
     "gadi_last_error", "gadi_solve_stencil_noalloc", "gadi_sweep", "gadi_model_fit",
     "gadi_model_predict", "gadi_model_loss", "gadi_mlp_gradient", "gadi_mlp_param_count",
-    "gadi_model_destroy", "gadi_set_model",
+    "gadi_model_destroy", "gadi_set_model", "gadi_sylv_create", "gadi_sylv_set_params", "gadi_sylv_solve",
+    "gadi_sylv_last_error", "gadi_sylv_destroy",
 ]
 GADI_MODEL_MLP, GADI_MODEL_GPR, GADI_MODEL_GRID = 0, 1, 2
 
@@ -125,6 +126,11 @@ def load(path: str = LIB_PATH):
         "gadi_mlp_param_count": (i32, []),
         "gadi_model_destroy": (None, [vp]),
         "gadi_set_model": (i32, [vp, i32, vp]),
+        "gadi_sylv_create": (i32, [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]),
+        "gadi_sylv_set_params": (i32, [vp, f64, f64, i32]),
+        "gadi_sylv_solve": (i32, [vp, vp, vp, f64, i32, C.POINTER(gadi_info)]),
+        "gadi_sylv_last_error": (C.c_char_p, [vp]),
+        "gadi_sylv_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -341,6 +347,46 @@ def gadi_model_destroy(model):
 
 def gadi_set_model(h, kind, model):
     _check(h, load().gadi_set_model(h, int(kind), model))
+
+
+# ---------------------------------------------------------------------------
+# GADI-AB for the Sylvester equation A X + X B = C
+# ---------------------------------------------------------------------------
+
+def gadi_sylv_create(a, b, stream=None):
+    """a, b = (lo, diag, up) host arrays of the tridiagonal A (m x m) and B (n x n)."""
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (*a, *b)]
+    m, n = len(arrs[1]), len(arrs[4])
+    if any(len(v) != m for v in arrs[:3]) or any(len(v) != n for v in arrs[3:]):
+        raise GadiError(GADI_ERR_INVALID_ARG, "lo, diag, up of one matrix must have equal lengths")
+    out = C.c_void_p()
+    st = load().gadi_sylv_create(m, n, *[v.ctypes.data for v in arrs], C.c_void_p(stream or 0), C.byref(out))
+    if st != GADI_OK:
+        raise GadiError(st, "gadi_sylv_create failed")
+    return out
+
+
+def _sylv_check(s, st):
+    if st != GADI_OK:
+        raise GadiError(st, load().gadi_sylv_last_error(s).decode())
+
+
+def gadi_sylv_set_params(s, alpha, omega, u_r=GADI_F16):
+    _sylv_check(s, load().gadi_sylv_set_params(s, float(alpha), float(omega), int(u_r)))
+
+
+def gadi_sylv_solve(s, Cm, X, tol=1e-13, max_outer=100000):
+    """Cm, X: torch CUDA float64 tensors (m x n, row-major). Returns (status, info)."""
+    info = gadi_info()
+    st = load().gadi_sylv_solve(s, C.c_void_p(_ptr(Cm)), C.c_void_p(_ptr(X)), float(tol), int(max_outer),
+                                C.byref(info))
+    if st in (GADI_ERR_INVALID_ARG, GADI_ERR_CUDA, GADI_ERR_OUT_OF_MEMORY):
+        raise GadiError(st, load().gadi_sylv_last_error(s).decode())
+    return st, info.as_dict()
+
+
+def gadi_sylv_destroy(s):
+    load().gadi_sylv_destroy(s)
 
 
 class Solver:
