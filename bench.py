@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-spmv", action="store_true", help="skip the operator bandwidth runs")
     ap.add_argument("--no-hbm", action="store_true", help="skip the 192^3 HBM-bound case")
     ap.add_argument("--no-ablation", action="store_true", help="skip the inner-precision ablation")
+    ap.add_argument("--no-sylvester", action="store_true", help="skip the Sylvester GADI-AB case")
     ap.add_argument("--workload", default=WORKLOAD, help="system of problems.WORKLOADS to time")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0,
                     help="bound on the CPU oracle's time for cpu_baseline")
@@ -365,6 +366,34 @@ def precision_ablation(G, h, b, x, alpha, omega, flush_l2, stream, torch):
     return out
 
 
+def sylvester_case(G, torch, m=1024, n=1024, r=0.1, alpha=0.05, omega=1.0):
+    """GADI-AB for the Sylvester equation of §4.3 (A = B = M + 2 r N + 100/(n+1)^2 I,
+    m = n = 1024, X* random, C = A X* + X* B): time to eta <= 1e-13 with FP16
+    and FP64 inner solves on the GPU (one warm-up solve each first)."""
+    import oracle
+    a = oracle.sylvester_matrices(m, r)
+    b = oracle.sylvester_matrices(n, r)
+    Xs = np.random.default_rng(0).standard_normal((m, n))
+    A, B = oracle.tri_dense(*a), oracle.tri_dense(*b)
+    Cm = torch.from_numpy(A @ Xs + Xs @ B).cuda()
+    out = {"m": m, "n": n, "r": r, "alpha": alpha, "omega": omega}
+    s = G.gadi_sylv_create(a, b)
+    try:
+        for name, u_r in (("fp16", G.GADI_F16), ("fp64", G.GADI_F64)):
+            G.gadi_sylv_set_params(s, alpha, omega, u_r)
+            X = torch.zeros_like(Cm)
+            G.gadi_sylv_solve(s, Cm, X, TOL)
+            X.zero_()
+            torch.cuda.synchronize()
+            st, info = G.gadi_sylv_solve(s, Cm, X, TOL)
+            err = float((X.cpu() - torch.from_numpy(Xs)).abs().max())
+            out[name] = {"status": G.status_str(st), "time_s": info["t_solve_s"], "outer_iters": info["outer_iters"],
+                         "eta_inf": info["eta_inf"], "max_abs_err_vs_exact": err}
+    finally:
+        G.gadi_sylv_destroy(s)
+    return out
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_2501_04229_gb300 import build as B
@@ -470,6 +499,9 @@ def run_gpu(args, rank, world):
                                     (("stencil", G.GADI_KERNEL_STENCIL),), flush_l2, stream))
         del p192
     G.gadi_set_kernel(h, kern)
+    sylv = None
+    if not args.no_sylvester and args.workload == WORKLOAD:
+        sylv = sylvester_case(G, torch)
     ablation = None
     if not args.no_ablation:
         ablation = precision_ablation(G, h, b, x, args.alpha, args.omega, flush_l2, stream, torch)
@@ -505,7 +537,7 @@ def run_gpu(args, rank, world):
     achieved = algorithmic_bytes(n, nnz, info, args.kernel, True) / statistics.mean(kern_t) / 1e9
     return {
         "ms_per_step": ms_per_step, "value": tot / args.steps, "info": info, "eta_gpu": eta_gpu,
-        "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(), "hbm_case": hbm_res, "ablation": ablation,
+        "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(), "hbm_case": hbm_res, "ablation": ablation, "sylvester": sylv,
         "e2e": statistics.mean(e2e), "predictor": predictor, "roofline": {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4),
@@ -614,6 +646,7 @@ def main():
         "spmv": r["spmv"],
         "hbm_case": r["hbm_case"],
         "precision_ablation": r["ablation"],
+        "sylvester_gadi_ab": r["sylvester"],
     })
     print(json.dumps(line))
 
