@@ -162,13 +162,16 @@ def reduce_max(value, world, device="cpu"):
     return float(t.item())
 
 
+# the sources the solve kernel and its launch are built from
+SOLVE_SOURCES = ("gadi_api.cu", "gadi_solve.cuh", "gadi_ops.cuh", "gadi_device.cuh", "gadi_bits.cuh")
+
+
 def kernel_source_digest():
-    import glob
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2501_04229_gb300", "csrc", "*.cu*"))):
-        h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+    for name in SOLVE_SOURCES:
+        h.update(name.encode())
+        h.update(open(os.path.join(ROOT, "paper_2501_04229_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
