@@ -175,19 +175,21 @@ def kernel_source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name):
-    """DRAM bytes per launch from a committed ncu summary, or None when the
-    kernel sources changed since that capture."""
+def profiled_traffic(name, algorithmic):
+    """DRAM bytes per launch from a committed ncu summary, scaled from the
+    profiled launch to this one by their algorithmic bytes (the same kernel on
+    the same system: traffic grows with the outer and inner steps), or None
+    when the kernel sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(path).read()
     except OSError:
         return None
-    fields = dict(line.split(":", 1) for line in txt.splitlines()
-                  if line.startswith(("kernel-source-sha256:", "dram-bytes-per-launch:")))
+    keys = ("kernel-source-sha256:", "dram-bytes-per-launch:", "algorithmic-bytes-per-launch:")
+    fields = dict(line.split(":", 1) for line in txt.splitlines() if line.startswith(keys))
     if fields.get("kernel-source-sha256", "").strip() != kernel_source_digest():
         return None
-    return float(fields["dram-bytes-per-launch"])
+    return round(float(fields["dram-bytes-per-launch"]) * algorithmic / float(fields["algorithmic-bytes-per-launch"]))
 
 
 def apply_bandwidth(G, torch, p, stencil, kernels, flush_l2, stream, reps=10):
@@ -311,7 +313,8 @@ def hbm_case(G, torch, P, predictor, args, flush_l2, stream, N, beta):
             kt.append(info["t_solve_s"])
         eta = info["eta_inf"]
         fwd = float((x.cpu() - torch.from_numpy(p.x_exact)).abs().max())
-        achieved = algorithmic_bytes(p.n, p.A.nnz, info, "stencil", True) / statistics.mean(kt) / 1e9
+        alg = algorithmic_bytes(p.n, p.A.nnz, info, "stencil", True)
+        achieved = alg / statistics.mean(kt) / 1e9
         peaks = {}
         try:
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -325,7 +328,8 @@ def hbm_case(G, torch, P, predictor, args, flush_l2, stream, N, beta):
                                            "grid_blocks", "block_threads")},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
-                         "traffic": profiled_traffic(f"gadi_solve_kernel_convdiff3d_{N}_b{beta:g}.md"),
+                         "traffic": profiled_traffic(f"gadi_solve_kernel_convdiff3d_{N}_b{beta:g}.md", alg),
+                         "algorithmic_bytes": alg,
                          "kernel": "gadi_solve_kernel<StencilOp<half,3,8>>",
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
         })
@@ -537,14 +541,17 @@ def run_gpu(args, rank, world):
     except OSError:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved = algorithmic_bytes(n, nnz, info, args.kernel, True) / statistics.mean(kern_t) / 1e9
+    alg = algorithmic_bytes(n, nnz, info, args.kernel, True)
+    achieved = alg / statistics.mean(kern_t) / 1e9
     return {
         "ms_per_step": ms_per_step, "value": tot / args.steps, "info": info, "eta_gpu": eta_gpu,
         "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(), "hbm_case": hbm_res, "ablation": ablation, "sylvester": sylv,
         "e2e": statistics.mean(e2e), "predictor": predictor, "roofline": {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4),
-            "traffic": profiled_traffic(f"gadi_solve_kernel_{args.workload}.md") if args.kernel == "stencil" else None,
+            "traffic": profiled_traffic(f"gadi_solve_kernel_{args.workload}.md", alg) if args.kernel == "stencil" else None,
+            "algorithmic_bytes": alg,
+            "traffic_note": "ncu dram bytes of the profiled launch, scaled to this launch by algorithmic bytes",
             "kernel": "gadi_solve_kernel<StencilOp<half,3,8>>" if args.kernel == "stencil"
             else "gadi_solve_kernel<EllOp<half>>",
             "note": "whole solve in one persistent launch; at 64^3 the working set is L2-resident, so this is an effective rate (the HBM-bound case is hbm_case)",
