@@ -51,12 +51,15 @@ __device__ __forceinline__ unsigned long long abs_bits(double v)
 }
 
 // R = C - A X - X B (fused multiply-adds in the order A's i-1, i, i+1, then
-// B's j-1, j, j+1); maxima of |R| (NaN above everything) and |X|
+// B's j-1, j, j+1); maxima of |R| (NaN above everything) and |X|. With R32,
+// also the round-to-odd FP32 copy of R: fl16(2^-e R) is then an exact FP32
+// scaling and one rounding (same bits as from FP64, for -100 <= e <= 126),
+// without FP64 work in the sequential solves.
 __global__ void k_residual(int64_t m, int64_t n, const double *__restrict__ al, const double *__restrict__ ad,
                            const double *__restrict__ au, const double *__restrict__ bl,
                            const double *__restrict__ bd, const double *__restrict__ bu,
                            const double *__restrict__ C, const double *__restrict__ X, double *__restrict__ R,
-                           unsigned long long *maxbits)
+                           float *__restrict__ R32, unsigned long long *maxbits)
 {
     unsigned long long rm = 0, xm = 0;
     const int64_t mn = m * n;
@@ -71,6 +74,7 @@ __global__ void k_residual(int64_t m, int64_t n, const double *__restrict__ al, 
         r = __fma_rn(-bd[j], x[0], r);
         if (j < n - 1) r = __fma_rn(-bl[j + 1], x[1], r);
         R[q] = r;
+        if (R32) R32[q] = __uint_as_float(float_bits_round_odd(r));
         rm = max(rm, abs_bits(r));
         xm = max(xm, abs_bits(x[0]));
     }
@@ -102,11 +106,13 @@ __device__ __forceinline__ int exp_of(const unsigned long long *bits, int low)
 
 // Tridiagonal solves along `count` lines of length len, line t at
 // base + t, elements stride apart (consecutive threads: consecutive
-// lines). FROM64: the right-hand side is fl_T(2^-e R) from the FP64 array
-// src; else the line already holds it (in T). Results (in T) go to dst.
+// lines). The right-hand side is fl_T(2^-e R): FROM = 1 from the FP64 array
+// src, FROM = 2 from its round-to-odd FP32 copy src32 (FP16 T); FROM = 0:
+// the line already holds it (in T). Results (in T) go to dst.
 // The maximum |result| goes to zmax (as float bits) when asked.
-template <class T, bool FROM64>
+template <class T, int FROM>
 __global__ void k_tri_lines(int64_t len, int64_t count, int64_t stride, const double *__restrict__ src,
+                            const float *__restrict__ src32,
                             T *__restrict__ dst, const typename Prec<T>::Acc *__restrict__ ls,
                             const typename Prec<T>::Acc *__restrict__ cf, const typename Prec<T>::Acc *__restrict__ iw,
                             const unsigned long long *rmaxbits, int low, unsigned *zmaxbits)
@@ -117,27 +123,57 @@ __global__ void k_tri_lines(int64_t len, int64_t count, int64_t stride, const do
     float zm = 0.0f;
     if (t < count) {
         double sc = 1.0;
-        if constexpr (FROM64) sc = ldexp(1.0, -exp_of(rmaxbits, low));
+        if constexpr (FROM != 0) sc = ldexp(1.0, -exp_of(rmaxbits, low));
+        const float sc32 = (float)sc;
         auto rhs = [&](int64_t i) -> Acc {
-            if constexpr (FROM64) {
+            if constexpr (FROM == 1) {
                 const double v = src[t + i * stride];
                 return P::ld(P::from64(sc == 1.0 ? v : v * sc));
+            } else if constexpr (FROM == 2) {
+                return P::rnd(__fmul_rn(src32[t + i * stride], sc32));
             } else {
                 return P::ld(dst[t + i * stride]);
             }
         };
-        Acc y = P::rnd(P::mul(rhs(0), iw[0]));
-        dst[t] = P::st(y);
-        for (int64_t i = 1; i < len; ++i) {
-            y = P::rnd(P::mul(P::madd(rhs(i), -ls[i], y), iw[i]));
-            dst[t + i * stride] = P::st(y);
+        // the recurrences run element by element; their operands are loaded
+        // KB at a time first, so a line's loads overlap instead of each one
+        // waiting for the previous step
+        constexpr int KB = 16;
+        Acc y = Acc(0);
+        for (int64_t i0 = 0; i0 < len; i0 += KB) {
+            Acc v[KB], l[KB], w[KB];
+#pragma unroll
+            for (int k = 0; k < KB; ++k)
+                if (i0 + k < len) {
+                    v[k] = rhs(i0 + k);
+                    l[k] = ls[i0 + k];
+                    w[k] = iw[i0 + k];
+                }
+#pragma unroll
+            for (int k = 0; k < KB; ++k)
+                if (i0 + k < len) {
+                    y = i0 + k == 0 ? P::rnd(P::mul(v[k], w[k])) : P::rnd(P::mul(P::madd(v[k], -l[k], y), w[k]));
+                    dst[t + (i0 + k) * stride] = P::st(y);
+                }
         }
         Acc z = y;
         zm = fabsf((float)z);
-        for (int64_t i = len - 2; i >= 0; --i) {
-            z = P::rnd(P::madd(P::ld(dst[t + i * stride]), -cf[i], z));
-            dst[t + i * stride] = P::st(z);
-            zm = fmaxf(zm, fabsf((float)z));
+        // back substitution over i = len-2 .. 0, in chunks [i1 - KB + 1, i1]
+        for (int64_t i1 = len - 2; i1 >= 0; i1 -= KB) {
+            Acc v[KB], c[KB];
+#pragma unroll
+            for (int k = 0; k < KB; ++k)
+                if (i1 - k >= 0) {
+                    v[k] = P::ld(dst[t + (i1 - k) * stride]);
+                    c[k] = cf[i1 - k];
+                }
+#pragma unroll
+            for (int k = 0; k < KB; ++k)
+                if (i1 - k >= 0) {
+                    z = P::rnd(P::madd(v[k], -c[k], z));
+                    dst[t + (i1 - k) * stride] = P::st(z);
+                    zm = fmaxf(zm, fabsf((float)z));
+                }
         }
     }
     if (zmaxbits) {
@@ -302,6 +338,9 @@ gadi_status run(gadi_sylv *s, const double *C, double *X, double tol, int max_ou
     const Acc *fla = fd, *fca = fd + m, *fiwa = fd + 2 * m;
     const Acc *flb = fd + 3 * m, *fcb = flb + n, *fiwb = flb + 2 * n;
     T *Z = (T *)s->Z, *Zt = (T *)s->Zt;
+    // FP16 only: below 2^-126 the FP32 copy is not exact, which bfloat16's range would show
+    constexpr bool k16 = std::is_same<T, __half>::value;
+    float *R32 = k16 ? reinterpret_cast<float *>(Zt) : nullptr;   // Zt is free until the transpose
     unsigned *zbits = reinterpret_cast<unsigned *>(s->maxbits + 3);
     const double pfac = (2.0 - s->omega) * s->alpha;
 
@@ -314,7 +353,7 @@ gadi_status run(gadi_sylv *s, const double *C, double *X, double tol, int max_ou
     for (;;) {
         SCK(cudaMemsetAsync(s->maxbits, 0, 2 * sizeof(unsigned long long), s->stream));   // max|R|, max|X|
         k_residual<<<grid_for(mn), kThreads, 0, s->stream>>>(m, n, s->al, s->ad, s->au, s->bl, s->bd, s->bu, C, X,
-                                                            s->R, s->maxbits);
+                                                            s->R, R32, s->maxbits);
         unsigned long long hb[3];
         SCK(cudaMemcpyAsync(hb, s->maxbits, sizeof hb, cudaMemcpyDeviceToHost, s->stream));
         SCK(cudaStreamSynchronize(s->stream));
@@ -328,11 +367,17 @@ gadi_status run(gadi_sylv *s, const double *C, double *X, double tol, int max_ou
         if (eta <= tol) { status = GADI_OK; break; }
         if (k >= max_outer) break;
         SCK(cudaMemsetAsync(zbits, 0, sizeof(unsigned), s->stream));
-        k_tri_lines<T, true><<<grid_for(n), kThreads, 0, s->stream>>>(m, n, n, s->R, Z, fla, fca, fiwa, s->maxbits,
-                                                                      low, zbits);
+        // one warp per block: the lines spread over as many SMs as there are warps of lines
+        const int e = (rmax > 0.0) ? std::ilogb(rmax) : 0;
+        if (k16 && e >= -100 && e <= 126)
+            k_tri_lines<T, 2><<<grid_for(n, 32), 32, 0, s->stream>>>(m, n, n, nullptr, R32, Z, fla, fca, fiwa,
+                                                                     s->maxbits, low, zbits);
+        else
+            k_tri_lines<T, 1><<<grid_for(n, 32), 32, 0, s->stream>>>(m, n, n, s->R, nullptr, Z, fla, fca, fiwa,
+                                                                     s->maxbits, low, zbits);
         k_transpose_scale<T><<<tg, tb, 0, s->stream>>>(m, n, Z, Zt, zbits, low);
-        k_tri_lines<T, false><<<grid_for(m), kThreads, 0, s->stream>>>(n, m, m, nullptr, Zt, flb, fcb, fiwb, nullptr,
-                                                                       low, nullptr);
+        k_tri_lines<T, 0><<<grid_for(m, 32), 32, 0, s->stream>>>(n, m, m, nullptr, nullptr, Zt, flb, fcb, fiwb,
+                                                                 nullptr, low, nullptr);
         k_update<T><<<tg, tb, 0, s->stream>>>(m, n, Zt, X, pfac, s->sA, s->sB, s->maxbits, zbits, low);
         SCK(cudaGetLastError());
         ++k;
