@@ -5,7 +5,8 @@
 Training records come from batched sweeps of small systems of the same
 structure (§3.3 trains on small systems): a 2D set (sides 16..128, beta
 log-uniform in [0.1, 1000]) and a 3D set (sides 8..48, beta log-uniform in
-[1, 500]), each swept over 16 alpha x 4 omega to eta_inf <= 1e-13. From each
+[1, 500]), each swept over 24 alpha in [0.01, 31.6] x 3 omega to eta_inf <=
+1e-13. From each
 set an MLP (trained on the GPU by the library's kernels) and a GPR are
 fitted. The test systems are the 3D convection-diffusion operator on an
 N^3 grid with beta log-uniform in [1, 500] (seeded, seeds 5000, 5001, ...)
@@ -35,7 +36,7 @@ EPS = 0.1
 
 
 def train_sets(seed=11):
-    cands = SW.candidates(n_alpha=16, omegas=SW.OMEGAS, lo=-1.5, hi=1.5)
+    cands = SW.candidates(n_alpha=24, omegas=(0.0, 0.5, 1.0), lo=-2.0, hi=1.5)
     sets = {}
     t0 = time.perf_counter()
     two = SW.random_instances(48, seed=seed, dim=2, side=(16, 128), beta=(0.1, 1000.0))
@@ -65,13 +66,13 @@ def solve(h, b, x, alpha, omega, max_outer=100000):
             "spmv_count": info["spmv_count"], "eta_inf": info["eta_inf"], "time_s": info["t_solve_s"]}
 
 
-def grid_optimum(h, b, x, n_alpha=12, omegas=(0.0, 0.5)):
+def grid_optimum(h, b, x, n_alpha=15, omegas=(0.0, 0.5, 1.0)):
     """Best (fewest operator applications) of an alpha x omega grid on the
-    case itself; each candidate is capped at 1.5x the outer steps of the best
-    one so far, and the grid is walked from alpha = 2 outwards so that a cap
-    exists early."""
+    case itself (alpha in [0.01, 31.6]); each candidate is capped at 1.5x the
+    outer steps of the best one so far, and the grid is walked from alpha =
+    0.3 outwards so that a cap exists early."""
     best, cap, tried = None, 100000, []
-    for a in sorted(SW.alpha_grid(n_alpha, -0.5, 1.5), key=lambda v: abs(math.log(v / 2.0))):
+    for a in sorted(SW.alpha_grid(n_alpha, -2.0, 1.5), key=lambda v: abs(math.log(v / 0.3))):
         for w in omegas:
             r = solve(h, b, x, a, w, max_outer=cap)
             tried.append(r)
