@@ -45,6 +45,7 @@ ALPHA, OMEGA = 3.0, 0.0          # best of an (alpha, omega, eps) sweep on this 
 EPS16 = 1e-1
 EPS64 = 1e-10
 HBM_ALPHA, HBM_OMEGA = 2.0, 0.0  # best of alpha in {2, 3, 4.5} on the 192^3 system
+GRF_ALPHA, GRF_OMEGA = 1.0, 1.0  # best of alpha in {0.03, 0.1, 0.3, 1} x omega in {0, 1} on the 128^3 GRF system
 
 
 def parse():
@@ -64,6 +65,7 @@ def parse():
     ap.add_argument("--no-hbm", action="store_true", help="skip the 192^3 HBM-bound case")
     ap.add_argument("--no-ablation", action="store_true", help="skip the inner-precision ablation")
     ap.add_argument("--no-sylvester", action="store_true", help="skip the Sylvester GADI-AB case")
+    ap.add_argument("--no-grf", action="store_true", help="skip the 128^3 variable-coefficient case")
     ap.add_argument("--workload", default=WORKLOAD, help="system of problems.WORKLOADS to time")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0,
                     help="bound on the CPU oracle's time for cpu_baseline")
@@ -373,6 +375,46 @@ def precision_ablation(G, h, b, x, alpha, omega, flush_l2, stream, torch):
     return out
 
 
+def grf_case(G, torch, P, flush_l2, stream, alpha=GRF_ALPHA, omega=GRF_OMEGA):
+    """The 128^3 system with GRF face coefficients (beta = 50): time to
+    eta_inf <= 1e-13 of FP16-inner GADI-IR with the face-coefficient stencil
+    kernel and with the general sparse (ELL) kernel, and plain FP64 GADI with
+    the stencil kernel, on the same GPU (one warm-up solve per kernel first;
+    L2 flushed before each timed solve)."""
+    p = P.workload("convdiff3d_128_b50_grf")
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
+    h = G.gadi_create(t(p.A.row_ptr, torch.int32), t(p.A.col_idx, torch.int32), t(p.A.val),
+                      stencil=(3, p.N, p.beta, 1), stream=stream.cuda_stream)
+    b = t(p.b)
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    out = {"workload": "convdiff3d_128_b50_grf", "n": p.n, "alpha": alpha, "omega": omega}
+    try:
+        for name, kern, u_r, eps, reps in (("fp16_stencil", G.GADI_KERNEL_STENCIL, G.GADI_F16, EPS16, 2),
+                                           ("fp16_sparse", G.GADI_KERNEL_SPARSE, G.GADI_F16, EPS16, 2),
+                                           ("fp64_gadi_stencil", G.GADI_KERNEL_STENCIL, G.GADI_F64, EPS64, 1)):
+            G.gadi_set_kernel(h, kern)
+            G.gadi_set_params(h, alpha, omega, u_r=u_r)
+            G.gadi_set_inner(h, eps, 500 if u_r == G.GADI_F16 else 10000, 100000)
+            for rep in range(reps):
+                x.zero_()
+                flush_l2()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st, info = G.gadi_solve(h, b, x, TOL)
+                e1.record(stream)
+                torch.cuda.synchronize()
+            out[name] = {"status": G.status_str(st), "time_s": e0.elapsed_time(e1) * 1e-3,
+                         "outer_iters": info["outer_iters"], "inner_iters_H": info["inner_iters_H"],
+                         "inner_iters_S": info["inner_iters_S"], "eta_inf": info["eta_inf"],
+                         "max_abs_err_vs_exact": float((x.cpu() - torch.from_numpy(p.x_exact)).abs().max())}
+        if out["fp16_stencil"]["status"] == "GADI_OK" and out["fp64_gadi_stencil"]["status"] == "GADI_OK":
+            out["speedup_fp16_vs_fp64_gadi"] = out["fp64_gadi_stencil"]["time_s"] / out["fp16_stencil"]["time_s"]
+    finally:
+        G.gadi_destroy(h)
+    return out
+
+
 def sylvester_case(G, torch, m=1024, n=1024, r=0.1, alpha=0.05, omega=1.0):
     """GADI-AB for the Sylvester equation of §4.3 (A = B = M + 2 r N + 100/(n+1)^2 I,
     m = n = 1024, X* random, C = A X* + X* B): time to eta <= 1e-13 with FP16
@@ -509,6 +551,9 @@ def run_gpu(args, rank, world):
     sylv = None
     if not args.no_sylvester and args.workload == WORKLOAD:
         sylv = sylvester_case(G, torch)
+    grf = None
+    if not args.no_grf and args.workload == WORKLOAD:
+        grf = grf_case(G, torch, P, flush_l2, stream)
     ablation = None
     if not args.no_ablation:
         ablation = precision_ablation(G, h, b, x, args.alpha, args.omega, flush_l2, stream, torch)
@@ -545,7 +590,7 @@ def run_gpu(args, rank, world):
     achieved = alg / statistics.mean(kern_t) / 1e9
     return {
         "ms_per_step": ms_per_step, "value": tot / args.steps, "info": info, "eta_gpu": eta_gpu,
-        "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(), "hbm_case": hbm_res, "ablation": ablation, "sylvester": sylv,
+        "x": x16, "p": p, "fp64": fp64, "spmv": spmv, "clocks": clocks.summary(), "hbm_case": hbm_res, "ablation": ablation, "sylvester": sylv, "grf": grf,
         "e2e": statistics.mean(e2e), "predictor": predictor, "roofline": {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4),
@@ -657,6 +702,7 @@ def main():
         "hbm_case": r["hbm_case"],
         "precision_ablation": r["ablation"],
         "sylvester_gadi_ab": r["sylvester"],
+        "grf_case": r["grf"],
     })
     print(json.dumps(line))
 
