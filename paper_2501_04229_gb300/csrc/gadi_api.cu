@@ -564,6 +564,7 @@ StencilOp<T, DIM, R> make_stencil(const gadi_solver *h)
     StencilOp<T, DIM, R> op{};
     op.dim = h->sdim;
     op.N = h->sN;
+    op.divN = div_magic((unsigned)op.N);
     op.n = h->n;
     op.a_diag = h->a_diag;
     op.a_lo = h->a_lo;

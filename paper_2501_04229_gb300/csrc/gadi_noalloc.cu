@@ -146,6 +146,7 @@ gadi_status launch(int dev, int num_sms, cudaStream_t stream, unsigned char *bas
     Op op{};
     op.dim = DIM;
     op.N = N;
+    op.divN = div_magic((unsigned)op.N);
     op.n = n;
     op.a_diag = a_diag;
     op.a_lo = a_lo;

@@ -369,6 +369,12 @@ struct EllOp {
 // (M is symmetric, so the lower coupling of node i along d is the upper
 // coupling of node i - e_d). N is the constant convection c in both forms.
 // ---------------------------------------------------------------------------
+// the multiplier of StencilOp::divide for side N
+__host__ __device__ inline unsigned long long div_magic(unsigned N)
+{
+    return N <= 1 ? 0ull : ~0ull / N + 1;
+}
+
 template <class T, int DIM, int RR>
 struct StencilOp {
     using Acc = typename Prec<T>::Acc;
@@ -392,14 +398,23 @@ struct StencilOp {
     // the diagonal's place in the row (zero otherwise: alpha is in sigS)
     Acc s_diag;
 
+    unsigned long long divN;          // ceil(2^64 / N) (0 for N = 1): v / N = mulhi(v, divN)
+
+    // v / N for v < 2^31: floor(v ceil(2^64/N) / 2^64) is exact, as the
+    // error v (ceil(2^64/N) N - 2^64) / (N 2^64) < 2^-33 stays below 1/N
+    __device__ __forceinline__ unsigned divide(unsigned v) const
+    {
+        return divN ? (unsigned)__umul64hi((unsigned long long)v, divN) : v;
+    }
+
     // grid coordinates of node i (x fastest); n < 2^31 is enforced at create
     __device__ __forceinline__ void coords(int64_t i, unsigned (&cd)[3]) const
     {
         const unsigned ii = (unsigned)i, NN = (unsigned)N;
-        const unsigned t = ii / NN;
+        const unsigned t = divide(ii);
         cd[0] = ii - t * NN;
         if (DIM == 3) {
-            const unsigned u = t / NN;
+            const unsigned u = divide(t);
             cd[1] = t - u * NN;
             cd[2] = u;
         } else {

@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(512, 1) gadi_sweep_kernel(const SweepArgs s)
         Op op{};
         op.dim = DIM;
         op.N = N;
+        op.divN = div_magic((unsigned)op.N);
         op.n = n;
         op.a_diag = a_diag;
         op.a_lo = a_lo;
