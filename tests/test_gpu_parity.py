@@ -455,6 +455,48 @@ def test_full_size_64cubed_workload_against_oracle():
     assert np.linalg.norm(x - p.x_exact) <= rn / lam + 1e-11
 
 
+def test_hbm_workload_192cubed_properties():
+    """The bench's HBM-bound system (192^3, n = 7.1e6) at full size, in the
+    launch configuration the bench times (automatic: 152 x 512): eta
+    recomputed by the oracle, and the forward error against the manufactured
+    solution within ||r||_2 / lambda_min(M) (A positive real)."""
+    p = P.workload("convdiff3d_192_b100")
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 2.0, 0.0)
+        G.gadi_set_inner(h, 0.1, 500, 100000)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK and info["grid_blocks"] * info["block_threads"] >= 152 * 256
+    finally:
+        G.gadi_destroy(h)
+    assert oracle.backward_error(p.A, p.b, x) <= 1e-13
+    lam = 3 * (2 - 2 * np.cos(np.pi / 193))
+    rn = np.linalg.norm(oracle.residual(p.A, p.b, x))
+    assert np.linalg.norm(x - p.x_exact) <= rn / lam + 1e-10
+
+
+def test_grf_128cubed_stencil_and_sparse_kernels():
+    """The variable-coefficient 128^3 system at full size with the
+    face-coefficient stencil kernel and the general sparse kernel: both reach
+    eta <= 1e-13 (recomputed by the oracle) and the manufactured solution."""
+    p = P.workload("convdiff3d_128_b50_grf")
+    xs = []
+    for kernel in (G.GADI_KERNEL_STENCIL, G.GADI_KERNEL_SPARSE):
+        h = _handle(p)
+        try:
+            G.gadi_set_params(h, 1.0, 1.0)
+            G.gadi_set_inner(h, 0.1, 500, 100000)
+            G.gadi_set_kernel(h, kernel)
+            st, info, x = _solve(h, p, 1e-13)
+            assert st == G.GADI_OK
+        finally:
+            G.gadi_destroy(h)
+        assert oracle.backward_error(p.A, p.b, x) <= 1e-13
+        assert np.abs(x - p.x_exact).max() <= 1e-8
+        xs.append(x)
+    assert np.abs(xs[0] - xs[1]).max() <= 1e-8
+
+
 def test_pure_diffusion_beta_zero():
     """beta = 0: N = 0, S = alpha I, so every CGNR solve takes one iteration."""
     p = P.make_problem(3, 16, 0.0)
