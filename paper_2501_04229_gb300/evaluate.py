@@ -13,7 +13,7 @@ N^3 grid with beta log-uniform in [1, 500] (seeded, seeds 5000, 5001, ...)
 and the manufactured right-hand side. For every case and predictor: the
 predicted (alpha, omega), the outer and inner iteration counts, operator
 applications and the time to eta_inf <= 1e-13 of FP16-inner GADI-IR, next to
-the best candidate of a grid search on the case itself (the judge of the
+the best candidate of a grid search on the case itself (the reference for the
 predictors' error).
 
 Prints a JSON summary and writes all records to --out.
