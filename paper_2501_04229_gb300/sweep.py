@@ -77,3 +77,39 @@ def run(instances, path=None, cands=None, chunk=16, **kw):
                 with open(path, "a") as f:
                     f.write(json.dumps(row) + "\n")
     return [done[(t[0], t[1], t[2])] for t in instances]
+
+
+def main(argv=None):
+    """Command line: sweep a seeded random instance set and append records.
+
+        python -m paper_2501_04229_gb300.sweep --count 256 --seed 4 --dim 2 \\
+            --side 64 1024 --beta 0.1 1000 --out records.jsonl
+
+    (the defaults: 256 2D instances, sides log-uniform in [64, 1024], beta
+    log-uniform in [0.1, 1000], 16 alpha x 4 omega, max_outer 5000)."""
+    import argparse
+    import time
+    from . import build
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--count", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--dim", type=int, default=2)
+    ap.add_argument("--side", type=int, nargs=2, default=(64, 1024))
+    ap.add_argument("--beta", type=float, nargs=2, default=(0.1, 1000.0))
+    ap.add_argument("--max-outer", type=int, default=5000)
+    ap.add_argument("--chunk", type=int, default=16)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args(argv)
+    build.build()
+    G.load()
+    inst = random_instances(args.count, args.seed, dim=args.dim, side=tuple(args.side), beta=tuple(args.beta))
+    t0 = time.perf_counter()
+    recs = run(inst, args.out, chunk=args.chunk, max_outer=args.max_outer)
+    dt = time.perf_counter() - t0
+    found = [r for r in recs if r["best"]]
+    print(json.dumps({"instances": len(recs), "with_best": len(found), "seconds": round(dt, 2),
+                      "n_max": max(r["n"] for r in recs), "sum_item_ms": round(sum(r["time_ms"] for r in recs), 1)}))
+
+
+if __name__ == "__main__":
+    main()
