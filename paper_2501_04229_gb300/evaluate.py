@@ -35,12 +35,19 @@ TOL = 1e-13
 EPS = 0.1
 
 
-def train_sets(seed=11):
+def train_sets(seed=11, records=None):
+    """The 2D training set: swept here (sides 16..128), or read from a record
+    file written by `python -m paper_2501_04229_gb300.sweep` (e.g. 256
+    instances with sides 64..1024); the 3D set is always swept here."""
     cands = SW.candidates(n_alpha=24, omegas=(0.0, 0.5, 1.0), lo=-2.0, hi=1.5)
     sets = {}
     t0 = time.perf_counter()
-    two = SW.random_instances(48, seed=seed, dim=2, side=(16, 128), beta=(0.1, 1000.0))
-    sets["2d"] = SW.run(two, cands=cands, eps_inner=EPS, max_outer=4000)
+    if records:
+        with open(records) as f:
+            sets["2d"] = [json.loads(line) for line in f]
+    else:
+        two = SW.random_instances(48, seed=seed, dim=2, side=(16, 128), beta=(0.1, 1000.0))
+        sets["2d"] = SW.run(two, cands=cands, eps_inner=EPS, max_outer=4000)
     three = SW.random_instances(40, seed=seed + 1, dim=3, side=(8, 48), beta=(1.0, 500.0))
     sets["3d"] = SW.run(three, cands=cands, eps_inner=EPS, max_outer=4000)
     return sets, time.perf_counter() - t0
@@ -88,11 +95,12 @@ def main(argv=None):
     ap.add_argument("--cases", type=int, default=8)
     ap.add_argument("--N", type=int, default=192)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--records", default=None, help="2D training records (JSONL) instead of a small sweep")
     args = ap.parse_args(argv)
     from . import build
     build.build()
     G.load()
-    sets, t_sweep = train_sets()
+    sets, t_sweep = train_sets(records=args.records)
     models = {}
     counts = {}
     for name, recs in sets.items():
