@@ -169,11 +169,17 @@ SOLVE_SOURCES = ("gadi_api.cu", "gadi_solve.cuh", "gadi_ops.cuh", "gadi_device.c
 
 
 def kernel_source_digest():
+    """Hash of the solve kernel's sources with comments and blank space
+    removed, so that a change of wording alone keeps a capture current."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in SOLVE_SOURCES:
+        text = open(os.path.join(ROOT, "paper_2501_04229_gb300", "csrc", name)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
         h.update(name.encode())
-        h.update(open(os.path.join(ROOT, "paper_2501_04229_gb300", "csrc", name), "rb").read())
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

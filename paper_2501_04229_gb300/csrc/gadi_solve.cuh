@@ -7,13 +7,16 @@
 // never leave the device.
 //
 // Outer step k:
-//   R   r = b - A x in FP64; ||r||_inf, ||r||_2^2, ||x||_inf; stopping test
+//   R   r = b - A x in FP64; ||r||_inf, ||r||_2^2, ||x||_inf; stopping test;
+//       the round-to-odd FP32 copy of r (FP16 inner path)
 //   D   e = floor(log2 ||r||_inf), r^ = fl_r(2^-e r) (§2.2: r^ = fl_r(s^));
 //       CG start u = H' r^
 //   CG  on H' = 2^-sM (aI + M): z ~ H'^-1 r^              (Alg. 1 step 2)
 //   C0  ez = floor(log2 ||z||_inf), z^ = 2^-ez z, s = S'^T z^
 //   CGNR on S' = 2^-sN (aI + N): y ~ S'^-1 z^            (Alg. 1 step 3)
-//   U   x += (2-w) a 2^(e - sM + ez - sN) y in FP64       (Alg. 1 step 4)
+//       each second pass also forms x + (2-w) a 2^(e - sM + ez - sN) y in
+//       FP64 into the other iterate buffer (Alg. 1 step 4); after the last
+//       pass that buffer holds the new iterate
 // With FP64 inner precision the scales are all 2^0.
 //
 // CG is the single-reduction (Chronopoulos-Gear) form: one exchange per
