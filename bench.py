@@ -611,6 +611,43 @@ def run_gpu(args, rank, world):
     }
 
 
+def host_info(n_doubles=1 << 26, reps=5):
+    """The host's CPU model and its memory copy rate (STREAM-style copy of a
+    512 MB FP64 array over all cores, bytes read + written per second, best
+    of reps), so that the oracle's time can be set against the host's own
+    bandwidth."""
+    import platform
+    import subprocess
+    from concurrent.futures import ThreadPoolExecutor
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    cores = os.cpu_count() or 1
+    src = np.ones(n_doubles)
+    dst = np.zeros(n_doubles)
+    bounds = np.linspace(0, n_doubles, cores + 1).astype(np.int64)
+    chunks = [(int(bounds[i]), int(bounds[i + 1])) for i in range(cores)]
+
+    def part(c):
+        np.copyto(dst[c[0]:c[1]], src[c[0]:c[1]])
+
+    best = float("inf")
+    with ThreadPoolExecutor(cores) as pool:
+        list(pool.map(part, chunks))
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            list(pool.map(part, chunks))
+            best = min(best, time.perf_counter() - t0)
+    return {"cpu_model": model, "host_copy_gbs": round(2 * 8 * n_doubles / best / 1e9, 1),
+            "host_copy_threads": cores}
+
+
 def cpu_oracle_time(p, alpha, omega, budget_s, name=WORKLOAD):
     """The oracle (FP64-inner GADI-IR, all host cores) on the same system,
     bounded: a full solve when it fits the budget, else max_outer steps
@@ -670,6 +707,7 @@ def main():
         v = statistics.mean(times)
         cb = dict(cb)
         cb["value"] = v
+        cb.update(host_info())
         line = dict(base, impl="reference", value=v, ms_per_step=v * 1e3, dtype="f64", config=cfg,
                     cpu_baseline=cb, e2e={"value": v, "unit": "s", "h2d_bytes_per_step": 0,
                                           "d2h_bytes_per_step": 0})
@@ -687,6 +725,7 @@ def main():
     if cb["value"] is None:
         cb["value"] = cb["per_outer_step_s"] * r["info"]["outer_iters"]
         cb["sample"] += f"; scaled to the GPU run's {r['info']['outer_iters']} outer steps"
+    cb.update(host_info())
     n = p.n
     line = dict(base)
     line.update({
