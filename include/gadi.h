@@ -59,7 +59,7 @@ typedef enum {
 
 typedef enum { GADI_SPLIT_HSS = 0, GADI_SPLIT_USER = 1 } gadi_splitting;
 
-typedef enum { GADI_F64 = 0, GADI_F32 = 1, GADI_F16 = 2, GADI_BF16 = 3 } gadi_precision;
+typedef enum { GADI_F64 = 0, GADI_F32 = 1, GADI_F16 = 2, GADI_BF16 = 3, GADI_E4M3 = 4 } gadi_precision;
 
 typedef enum {
     GADI_STOP_ETA = 0,   /* stop when eta_inf = ||b-Ax||_inf/(||A||_inf ||x||_inf + ||b||_inf) <= tol */
@@ -139,17 +139,21 @@ GADI_API gadi_status gadi_create(const gadi_csr *A, gadi_splitting split, const 
  * with FP32 arithmetic (one fused multiply-add per product-sum); A, r and z
  * are scaled by powers of two so FP16 stays in range, and (2 - omega) alpha
  * is applied in the FP64 update. u_r = GADI_BF16: the same with bfloat16
- * storage (8 significant bits). u_r = GADI_F32: FP32 storage and arithmetic,
- * r and z scaled, the operators not. u_r = GADI_F64 with the default inner
- * tolerance is plain FP64 GADI. */
+ * storage (8 significant bits). u_r = GADI_E4M3: the same with FP8 E4M3
+ * storage (4 significant bits, largest finite value 448; stores round to
+ * nearest even and saturate at +-448); a precision below the paper's FP16.
+ * u_r = GADI_F32: FP32 storage and arithmetic, r and z scaled, the
+ * operators not. u_r = GADI_F64 with the default inner tolerance is plain
+ * FP64 GADI. RANGE when a nonzero matrix entry of the scaled inner operators
+ * rounds to zero in u_r. */
 GADI_API gadi_status gadi_set_params(gadi_solver *h, double alpha, double omega,
                             gadi_precision u_r, gadi_precision u, gadi_precision u_f);
 
 /* Inner relative tolerance eps (0 < eps < 1): each inner solve stops when
  * ||rhs - K v||_2 <= eps ||rhs||_2, or after max_inner iterations (>= 1).
- * max_outer (>= 0) caps the refinement steps. Defaults: eps 1e-2 (inner
- * precision below FP64) / 1e-10 (FP64 inner), max_inner 200, max_outer
- * 100000. */
+ * max_outer (>= 0) caps the refinement steps. Defaults: eps 1e-2 (FP32,
+ * FP16 and bfloat16 inner precision) / 0.1 (FP8 E4M3) / 1e-10 (FP64 inner),
+ * max_inner 200, max_outer 100000. */
 GADI_API gadi_status gadi_set_inner(gadi_solver *h, double eps_inner, int32_t max_inner, int32_t max_outer);
 
 /* Stopping criterion kind for gadi_solve's tol (default GADI_STOP_ETA). */
@@ -209,11 +213,12 @@ GADI_API gadi_status gadi_solve(gadi_solver *h, const double *b, double *x, doub
 /* One operator application with the solver's current kernel and parameters,
  * y = K x, for kernel-level tests and bandwidth measurement. which:
  *   0: K = A      (FP64 x, y)
- *   1: K = H' = 2^-sM (aI + M)  in the inner precision (x, y FP16 or FP64)
+ *   1: K = H' = 2^-sM (aI + M)  in the inner precision
  *   2: K = S' = 2^-sN (aI + N)
  *   3: K = S'^T
  * x, y are device pointers of n elements of the inner precision (FP64 for
- * which = 0; FP16, bfloat16, FP32 or FP64 after gadi_set_params' u_r).
+ * which = 0; FP16, bfloat16, FP8 E4M3 (one byte each), FP32 or FP64 after
+ * gadi_set_params' u_r).
  * Asynchronous on the handle's stream. */
 GADI_API gadi_status gadi_apply(gadi_solver *h, int32_t which, const void *x, void *y);
 
@@ -369,7 +374,8 @@ GADI_API gadi_status gadi_sylv_create(int64_t m, int64_t n, const double *a_lo, 
                                       const double *a_up, const double *b_lo, const double *b_diag,
                                       const double *b_up, void *cuda_stream, gadi_sylv **out);
 
-/* alpha > 0, omega in [0, 2) (Thm 1), u_r any gadi_precision. */
+/* alpha > 0, omega in [0, 2) (Thm 1), u_r = GADI_F64, GADI_F32, GADI_F16
+ * or GADI_BF16 (GADI_E4M3: UNSUPPORTED). */
 GADI_API gadi_status gadi_sylv_set_params(gadi_sylv *s, double alpha, double omega, gadi_precision u_r);
 
 /* Solve in place: C and X are device pointers to row-major m x n FP64

@@ -27,7 +27,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PREC_DOUBLE, PREC_SINGLE, PREC_HALF, PREC_HALF_NAIVE, PREC_BF16 = 0, 1, 2, 3, 4
+PREC_DOUBLE, PREC_SINGLE, PREC_HALF, PREC_HALF_NAIVE, PREC_BF16, PREC_E4M3 = 0, 1, 2, 3, 4, 5
 STOP_ETA, STOP_RES = 0, 1
 OK, INVALID, OOM, NOT_CONVERGED, DIVERGED = 0, 1, 2, 5, 6
 
@@ -69,6 +69,7 @@ def _load():
     build()
     lib = C.CDLL(_LIB_PATH)
     p_i32, p_f64, p_u16 = C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_uint16)
+    p_u8 = C.POINTER(C.c_uint8)
     i64, f64 = C.c_int64, C.c_double
     sig = {
         "or_set_threads": (None, [C.c_int]),
@@ -90,6 +91,7 @@ def _load():
                                   p_f64, p_f64, p_i32, p_i32]),
         "or_to_half_bits": (None, [i64, p_f64, p_u16]),
         "or_to_bf16_bits": (None, [i64, p_f64, p_u16]),
+        "or_to_e4m3_bits": (None, [i64, p_f64, p_u8]),
         "or_sylv_norm_inf": (f64, [i64, i64, p_f64, p_f64, p_f64, p_f64, p_f64, p_f64]),
         "or_sylv_gadi_ab": (C.c_int, [i64, i64, p_f64, p_f64, p_f64, p_f64, p_f64, p_f64, p_f64, p_f64,
                                   f64, f64, C.c_int32, f64, C.c_int32, C.POINTER(Info), p_f64]),
@@ -308,6 +310,15 @@ def to_bf16_bits(x) -> np.ndarray:
     x = _f64(x)
     out = np.empty(x.shape, dtype=np.uint16)
     _load().or_to_bf16_bits(x.size, _p(x, C.c_double), _p(out, C.c_uint16))
+    return out
+
+
+def to_e4m3_bits(x) -> np.ndarray:
+    """FP8 E4M3 codes of fl_e4m3(x): round to nearest even from FP64,
+    saturating at +-448."""
+    x = _f64(x)
+    out = np.empty(x.shape, dtype=np.uint8)
+    _load().or_to_e4m3_bits(x.size, _p(x, C.c_double), _p(out, C.c_uint8))
     return out
 
 

@@ -23,6 +23,9 @@
  *     paper's experiments);
  *   - bfloat16 inner precision: as FP16 (scaled the same way), with 8
  *     significant bits and FP32's exponent range;
+ *   - FP8 E4M3 inner precision (below the paper's FP16; its future-work
+ *     direction): as FP16, with 4 significant bits, largest finite value
+ *     448 and saturating rounding;
  *   - FP16 inner precision ("half"): FP16 storage of matrix values and inner
  *     vectors, FP32 arithmetic; the matrix, the residual and the first
  *     correction are scaled by powers of two so that FP16 stays in range; the
@@ -57,7 +60,8 @@
 /* loops over fewer elements than this run on one thread */
 #define OR_PAR_MIN 32768
 
-enum { OR_PREC_DOUBLE = 0, OR_PREC_SINGLE = 1, OR_PREC_HALF = 2, OR_PREC_HALF_NAIVE = 3, OR_PREC_BF16 = 4 };
+enum { OR_PREC_DOUBLE = 0, OR_PREC_SINGLE = 1, OR_PREC_HALF = 2, OR_PREC_HALF_NAIVE = 3, OR_PREC_BF16 = 4,
+       OR_PREC_E4M3 = 5 };
 enum { OR_STOP_ETA = 0, OR_STOP_RES = 1 };
 
 typedef struct {
@@ -327,9 +331,32 @@ int64_t or_cgnr(int64_t n, const int32_t *rp, const int32_t *ci, const double *v
 /* ------------------------------------------------------------------ */
 
 /* Storage rounding of the low-precision modes: rt = 0 FP32 (none), 1 FP16,
- * 2 bfloat16 (8 significant bits, FP32's exponent range), all round to
- * nearest even. */
-enum { RT_F32 = 0, RT_F16 = 1, RT_BF16 = 2 };
+ * 2 bfloat16 (8 significant bits, FP32's exponent range), 3 FP8 E4M3, all
+ * round to nearest even. */
+enum { RT_F32 = 0, RT_F16 = 1, RT_BF16 = 2, RT_E4M3 = 3 };
+
+/* FP8 E4M3 (the OCP 8-bit floating-point format): a sign bit, 4 exponent
+ * bits with bias 7 and 3 fraction bits. Exponent field 0 holds the
+ * subnormals m 2^-9 (m = 0..7); there is no infinity and only the all-ones
+ * pattern is NaN, so the largest finite magnitude is 1.75 2^8 = 448.
+ * v is rounded to the nearest representable value, ties to the even
+ * fraction; magnitudes beyond 448 saturate to 448 (the saturating
+ * conversion an inner storage needs: no value becomes NaN). */
+static double e4m3_of_double(double v)
+{
+    if (v != v) return v;
+    const double a = fabs(v);
+    if (a >= 448.0) return copysign(448.0, v);
+    /* spacing of the representable values near a: 2^-9 below 2^-5, then
+     * 2^(e-3) on [2^e, 2^(e+1)) */
+    double ulp = ldexp(1.0, -9);
+    while (ulp * 16.0 <= a) ulp *= 2.0;
+    const double k = a / ulp;                    /* exact: ulp is a power of two */
+    double f = floor(k);
+    const double rem = k - f;
+    if (rem > 0.5 || (rem == 0.5 && fmod(f, 2.0) != 0.0)) f += 1.0;
+    return copysign(f * ulp, v);
+}
 
 static inline float bf16_of_float(float x)
 {
@@ -363,12 +390,14 @@ static inline float float_round_odd(double x)
 
 static inline float rnd_store(float x, int rt)
 {
+    if (rt == RT_E4M3) return (float)e4m3_of_double((double)x);
     return rt == RT_F16 ? (float)(_Float16)x : (rt == RT_BF16 ? bf16_of_float(x) : x);
 }
 
 /* an FP64 value rounded once to the storage precision */
 static inline float rnd_from64(double v, int rt)
 {
+    if (rt == RT_E4M3) return (float)e4m3_of_double(v);
     return rt == RT_F16 ? (float)(_Float16)v : (rt == RT_BF16 ? bf16_of_float(float_round_odd(v)) : (float)v);
 }
 
@@ -630,7 +659,7 @@ int or_gadi_ir_split(int64_t n, const int32_t *rp, const int32_t *ci, const doub
                      or_info *info, double *eta_hist, int32_t *itH, int32_t *itS)
 {
     memset(info, 0, sizeof(*info));
-    if (check_params(P) != OR_OK || P->inner_prec < 0 || P->inner_prec > OR_PREC_BF16) {
+    if (check_params(P) != OR_OK || P->inner_prec < 0 || P->inner_prec > OR_PREC_E4M3) {
         info->status = OR_INVALID; return OR_INVALID;
     }
     int64_t nnz = rp[n];
@@ -648,8 +677,9 @@ int or_gadi_ir_split(int64_t n, const int32_t *rp, const int32_t *ci, const doub
     const double al = P->alpha, om = P->omega, pfac = (2.0 - om) * al;
     const int prec = P->inner_prec;
     const int naive = (prec == OR_PREC_HALF_NAIVE);
-    /* storage rounding; the FP16 and bfloat16 modes scale the operators */
-    const int rt = (prec == OR_PREC_HALF || naive) ? RT_F16 : (prec == OR_PREC_BF16 ? RT_BF16 : RT_F32);
+    /* storage rounding; the FP16, bfloat16 and FP8 modes scale the operators */
+    const int rt = (prec == OR_PREC_HALF || naive) ? RT_F16
+                   : (prec == OR_PREC_BF16 ? RT_BF16 : (prec == OR_PREC_E4M3 ? RT_E4M3 : RT_F32));
     const int half = (rt != RT_F32);
 
     double *r = (double *)malloc(szv), *z = (double *)malloc(szv), *y = (double *)malloc(szv);
@@ -784,7 +814,8 @@ int or_gadi_ir(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
  *   which 1: y = fl(H' x),  H' = 2^-sM (aI + M)
  *   which 2: y = fl(S' x),  S' = 2^-sN (aI + N)
  *   which 3: y = fl(S'^T x)
- * prec: OR_PREC_HALF, OR_PREC_HALF_NAIVE, OR_PREC_SINGLE or OR_PREC_DOUBLE;
+ * prec: OR_PREC_HALF, OR_PREC_HALF_NAIVE, OR_PREC_BF16, OR_PREC_E4M3,
+ * OR_PREC_SINGLE or OR_PREC_DOUBLE;
  * x holds values of that precision (as doubles). The scale exponents used
  * are returned (zero in the naive mode, where alpha is rounded into the
  * stored FP16 diagonal as in or_gadi_ir_split). */
@@ -803,7 +834,8 @@ int or_lp_apply(int64_t n, const int32_t *rp, const int32_t *ci, const double *a
     int32_t *rpt, *cit; double *nvt;
     transpose_csr(n, rp, ci, nv, &rpt, &cit, &nvt);
     const int naive = prec == OR_PREC_HALF_NAIVE;
-    const int rt = (prec == OR_PREC_HALF || naive) ? RT_F16 : (prec == OR_PREC_BF16 ? RT_BF16 : RT_F32);
+    const int rt = (prec == OR_PREC_HALF || naive) ? RT_F16
+                   : (prec == OR_PREC_BF16 ? RT_BF16 : (prec == OR_PREC_E4M3 ? RT_E4M3 : RT_F32));
     const int half = rt != RT_F32;
     int sM = 0, sN = 0;
     if (half && !naive) {
@@ -862,6 +894,29 @@ void or_to_bf16_bits(int64_t n, const double *in, uint16_t *out)
         uint32_t u;
         memcpy(&u, &f, sizeof u);
         out[i] = (uint16_t)(u >> 16);
+    }
+}
+
+/* FP64 -> FP8 E4M3 (round to nearest even, saturating), as the 8-bit
+ * codes: sign << 7 | exponent field << 3 | fraction; NaN as 0x7f. */
+void or_to_e4m3_bits(int64_t n, const double *in, uint8_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const double r = e4m3_of_double(in[i]);
+        if (r != r) { out[i] = 0x7f; continue; }
+        const uint8_t sign = signbit(r) ? 0x80 : 0x00;
+        const double a = fabs(r);
+        uint8_t code;
+        if (a < ldexp(1.0, -6)) {
+            code = (uint8_t)(a / ldexp(1.0, -9));               /* subnormal: m 2^-9 */
+        } else {
+            int e = 0;
+            frexp(a, &e);                                        /* a in [2^(e-1), 2^e) */
+            const int ex = e - 1;
+            const int frac = (int)(a / ldexp(1.0, ex - 3)) - 8;  /* a = (8 + frac) 2^(ex-3) */
+            code = (uint8_t)(((ex + 7) << 3) | frac);
+        }
+        out[i] = sign | code;
     }
 }
 

@@ -454,8 +454,8 @@ gadi_status count_lost(gadi_solver *h, const TD *m, const TD *nv, const char *na
 }
 
 // Demote the inner operators for the current alpha and inner precision:
-// FP16 and bfloat16 with the power-of-two scaling (or FP16 unscaled), FP32
-// unscaled; FP64 needs nothing.
+// FP16, bfloat16 and FP8 E4M3 with the power-of-two scaling (or FP16
+// unscaled), FP32 unscaled; FP64 needs nothing.
 gadi_status prepare_inner(gadi_solver *h)
 {
     if (h->u_r == GADI_F64) {
@@ -496,12 +496,19 @@ gadi_status prepare_inner(gadi_solver *h)
             demote_all<__half>(h, h->m16, h->n16, h->nt16, h->HD16, h->HK16, naive, scM, scN);
             CK(cudaGetLastError());
             st = count_lost<__half>(h, h->m16, h->n16, "FP16");
-        } else {
+        } else if (h->u_r == GADI_BF16) {
             auto bf = [](__half *p) { return reinterpret_cast<__nv_bfloat16 *>(p); };
             __nv_bfloat16 *hk[3] = {bf(h->HK16[0]), bf(h->HK16[1]), bf(h->HK16[2])};
             demote_all<__nv_bfloat16>(h, bf(h->m16), bf(h->n16), bf(h->nt16), bf(h->HD16), hk, false, scM, scN);
             CK(cudaGetLastError());
             st = count_lost<__nv_bfloat16>(h, bf(h->m16), bf(h->n16), "bfloat16");
+        } else {
+            // one-byte values in the first half of the 2-byte arrays
+            auto f8 = [](__half *p) { return reinterpret_cast<__nv_fp8_e4m3 *>(p); };
+            __nv_fp8_e4m3 *hk[3] = {f8(h->HK16[0]), f8(h->HK16[1]), f8(h->HK16[2])};
+            demote_all<__nv_fp8_e4m3>(h, f8(h->m16), f8(h->n16), f8(h->nt16), f8(h->HD16), hk, false, scM, scN);
+            CK(cudaGetLastError());
+            st = count_lost<__nv_fp8_e4m3>(h, f8(h->m16), f8(h->n16), "FP8 E4M3");
         }
     }
     if (st != GADI_OK) return st;
@@ -547,12 +554,28 @@ float half_round(double v)
     return __half2float(__double2half(v));
 }
 
+// v rounded to the nearest FP8 E4M3 value: 3 fraction bits below the
+// leading bit, whose exponent is at least -6 (the smallest normal exponent;
+// below it the spacing stays 2^-9), ties to even; magnitudes at or above
+// 448, the largest finite value, saturate to it
+float e4m3_round(double v)
+{
+    if (std::isnan(v)) return (float)v;
+    const double a = std::fabs(v);
+    if (a >= 448.0) return (float)std::copysign(448.0, v);
+    int ex = 0;
+    std::frexp(a, &ex);                        // a = f 2^ex, f in [0.5, 1)
+    const double q = std::ldexp(1.0, std::max(ex - 1, -6) - 3);
+    return (float)std::copysign(std::nearbyint(a / q) * q, v);
+}
+
 // v rounded once to the inner storage type T (as an arithmetic value)
 template <class T>
 typename Prec<T>::Acc round_to(double v)
 {
     if constexpr (std::is_same<T, __half>::value) return half_round(v);
     else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __bfloat162float(__double2bfloat16(v));
+    else if constexpr (std::is_same<T, __nv_fp8_e4m3>::value) return e4m3_round(v);
     else if constexpr (std::is_same<T, float>::value) return (float)v;
     else return v;
 }
@@ -671,7 +694,7 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     a.anorm = h->anorm;
     a.bnorm = bnorm;
     a.tol = tol;
-    a.eps = h->eps > 0 ? h->eps : (h->u_r == GADI_F64 ? 1e-10 : 1e-2);
+    a.eps = h->eps > 0 ? h->eps : (h->u_r == GADI_F64 ? 1e-10 : (h->u_r == GADI_E4M3 ? 0.1 : 1e-2));
     a.pfac = (2.0 - h->omega) * h->alpha;
     a.sM = h->sM;
     a.sN = h->sNs;
@@ -783,6 +806,7 @@ gadi_status dispatch(const gadi_solver *h, Fn &&fn)
     switch (h->u_r) {
     case GADI_F16: return dispatch_op<__half>(h, fn);
     case GADI_BF16: return dispatch_op<__nv_bfloat16>(h, fn);
+    case GADI_E4M3: return dispatch_op<__nv_fp8_e4m3>(h, fn);
     case GADI_F32: return dispatch_op<float>(h, fn);
     default: return dispatch_op<double>(h, fn);
     }
@@ -993,7 +1017,7 @@ gadi_status gadi_set_params(gadi_solver *h, double alpha, double omega, gadi_pre
         return fail(h, GADI_ERR_INVALID_ARG, "alpha must be positive and finite (Thm 1)");
     if (!(omega >= 0.0 && omega < 2.0))
         return fail(h, GADI_ERR_INVALID_ARG, "omega must lie in [0, 2) (Thm 1)");
-    auto valid = [](int p) { return p >= GADI_F64 && p <= GADI_BF16; };
+    auto valid = [](int p) { return p >= GADI_F64 && p <= GADI_E4M3; };
     if (!valid(u_r) || !valid(u) || !valid(u_f))
         return fail(h, GADI_ERR_INVALID_ARG, "unknown precision");
     if (u != GADI_F64 || u_f != GADI_F64)

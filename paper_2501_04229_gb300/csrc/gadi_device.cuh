@@ -5,6 +5,9 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <type_traits>
 
 #include "gadi_bits.cuh"
 #include <stdint.h>
@@ -210,6 +213,74 @@ template <> struct Prec<__nv_bfloat16> {
         }
     }
 };
+
+// FP8 E4M3 storage with FP32 arithmetic (a precision variant of u_r below
+// the paper's FP16): 3 fraction bits, exponent bias 7, largest finite value
+// 448, subnormals down to 2^-9. Stores round to nearest even and saturate
+// at +-448 (the format has no infinity).
+template <> struct Prec<__nv_fp8_e4m3> {
+    using Acc = float;
+    static __device__ __forceinline__ float ld(__nv_fp8_e4m3 v)
+    {
+        return __half2float(__half(__nv_cvt_fp8_to_halfraw(v.__x, __NV_E4M3)));
+    }
+    static __device__ __forceinline__ __nv_fp8_e4m3 st(float v)
+    {
+        __nv_fp8_e4m3 o;
+        o.__x = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+        return o;
+    }
+    static __device__ __forceinline__ float rnd(float v) { return ld(st(v)); }
+    // one rounding from FP64: round to odd at FP32 first (24 >= 4 + 2 bits)
+    static __device__ __forceinline__ __nv_fp8_e4m3 from64(double v)
+    {
+        return st(__uint_as_float(float_bits_round_odd(v)));
+    }
+    static __device__ __forceinline__ double to64(float v) { return double_of_float(v); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float madd(float c, float a, float b) { return __fmaf_rn(a, b, c); }
+    template <int K>
+    static __device__ __forceinline__ void madd_s(float (&o)[K], const float (&c)[K], float a, const float (&b)[K])
+    {
+        Prec<__half>::madd_s(o, c, a, b);
+    }
+    template <int K>
+    static __device__ __forceinline__ void madd_v(float (&o)[K], const float (&c)[K], const float (&a)[K],
+                                                  const float (&b)[K])
+    {
+        Prec<__half>::madd_v(o, c, a, b);
+    }
+    template <int K>
+    static __device__ __forceinline__ void mul_s(float (&o)[K], float a, const float (&b)[K])
+    {
+        Prec<__half>::mul_s(o, a, b);
+    }
+    // two values per conversion each way (FP8 pairs widen exactly to FP16)
+    template <int K>
+    static __device__ __forceinline__ void rndv(float (&v)[K])
+    {
+        if constexpr (K % 2 == 0) {
+#pragma unroll
+            for (int k = 0; k < K; k += 2) {
+                const __nv_fp8x2_storage_t q =
+                    __nv_cvt_float2_to_fp8x2(make_float2(v[k], v[k + 1]), __NV_SATFINITE, __NV_E4M3);
+                const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(q, __NV_E4M3)));
+                v[k] = f.x;
+                v[k + 1] = f.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = rnd(v[k]);
+        }
+    }
+};
+
+// storage types whose demotion of r (Alg. 1 step 2) starts from the
+// round-to-odd FP32 copy of r: FP16 and FP8 (24 >= 11 + 2 and 24 >= 4 + 2)
+template <class T>
+constexpr bool kDemoteFromOdd = std::is_same<T, __half>::value || std::is_same<T, __nv_fp8_e4m3>::value;
 
 template <> struct Prec<double> {
     using Acc = double;

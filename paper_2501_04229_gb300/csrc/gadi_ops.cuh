@@ -119,6 +119,45 @@ __device__ __forceinline__ void stv(__nv_bfloat16 *p, int64_t j0, const float (&
     }
 }
 
+// FP8 E4M3 chunks: one 4- or 8-byte transaction; element j0 + k is byte k
+// (little endian), pairs convert through FP16 (exact)
+template <int K>
+__device__ __forceinline__ void ldv(const __nv_fp8_e4m3 *p, int64_t j0, float (&o)[K])
+{
+    static_assert(K == 4 || K == 8, "chunk width");
+    uint32_t w[K / 4];
+    if constexpr (K == 8) {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p + j0);
+        w[0] = u.x;
+        w[1] = u.y;
+    } else {
+        w[0] = *reinterpret_cast<const uint32_t *>(p + j0);
+    }
+#pragma unroll
+    for (int k = 0; k < K / 2; ++k) {
+        const __nv_fp8x2_storage_t q = (__nv_fp8x2_storage_t)(w[k / 2] >> (16 * (k % 2)));
+        const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(q, __NV_E4M3)));
+        o[2 * k] = f.x;
+        o[2 * k + 1] = f.y;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void stv(__nv_fp8_e4m3 *p, int64_t j0, const float (&v)[K])
+{
+    uint32_t w[K / 4];
+#pragma unroll
+    for (int k = 0; k < K / 4; ++k) w[k] = 0u;
+#pragma unroll
+    for (int k = 0; k < K / 2; ++k) {
+        const __nv_fp8x2_storage_t q =
+            __nv_cvt_float2_to_fp8x2(make_float2(v[2 * k], v[2 * k + 1]), __NV_SATFINITE, __NV_E4M3);
+        w[k / 2] |= (uint32_t)q << (16 * (k % 2));
+    }
+    if constexpr (K == 8) *reinterpret_cast<uint2 *>(p + j0) = make_uint2(w[0], w[1]);
+    else *reinterpret_cast<uint32_t *>(p + j0) = w[0];
+}
+
 template <int K>
 __device__ __forceinline__ void ldv(const float *p, int64_t j0, float (&o)[K])
 {
@@ -282,16 +321,17 @@ struct XDemote {                     // fl_T(2^-e r), r in FP64 (Alg. 1: r^ = fl
     }
 };
 
-// fl16(2^-e r) from the round-to-odd FP32 copy of r: an exact FP32 scaling
-// and one round-to-nearest-even conversion give the same FP16 value as the
-// direct conversion from FP64 (valid for -100 <= e <= 126, where entries
-// below the FP32 normal range round to zero either way)
+// fl_T(2^-e r) (T = FP16 or FP8) from the round-to-odd FP32 copy of r: an
+// exact FP32 scaling and one round-to-nearest-even conversion give the same
+// value as the direct conversion from FP64 (valid for -100 <= e <= 126,
+// where entries below the FP32 normal range round to zero either way)
+template <class T>
 struct XDemoteOdd {
     const float *r32;
     float sc;                        // 2^-e
     __device__ __forceinline__ float one(int64_t j) const
     {
-        return __half2float(__float2half_rn(__fmul_rn(r32[j], sc)));
+        return Prec<T>::rnd(__fmul_rn(r32[j], sc));
     }
     template <int K>
     __device__ __forceinline__ void many(int64_t j0, float (&o)[K]) const
@@ -299,7 +339,7 @@ struct XDemoteOdd {
         float x[K];
         ldv<K>(r32, j0, x);
         Prec<__half>::mul_s(x, sc, x);
-        Prec<__half>::rndv(x);
+        Prec<T>::rndv(x);
 #pragma unroll
         for (int k = 0; k < K; ++k) o[k] = x[k];
     }

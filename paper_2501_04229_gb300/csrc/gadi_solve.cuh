@@ -8,7 +8,7 @@
 //
 // Outer step k:
 //   R   r = b - A x in FP64; ||r||_inf, ||r||_2^2, ||x||_inf; stopping test;
-//       the round-to-odd FP32 copy of r (FP16 inner path)
+//       the round-to-odd FP32 copy of r (FP16 and FP8 inner paths)
 //   D   e = floor(log2 ||r||_inf), r^ = fl_r(2^-e r) (§2.2: r^ = fl_r(s^));
 //       CG start u = H' r^
 //   CG  on H' = 2^-sM (aI + M): z ~ H'^-1 r^              (Alg. 1 step 2)
@@ -41,7 +41,7 @@ struct SolveArgs {
     double *x;                   // in: x0, out: the result
     double *x2;                  // n doubles: the iterates alternate between x and x2
     double *r64;
-    float *r32;                  // n floats: round-to-odd copy of r (FP16 inner path)
+    float *r32;                  // n floats: round-to-odd copy of r (FP16 / FP8 inner paths)
     T *v[9];                     // inner work vectors, n elements each
     double anorm, bnorm, tol, eps, pfac;
     int sM, sN, stop_kind;
@@ -110,7 +110,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
                     xmax = fmax(xmax, fabs(xx[q]));
                 }
                 IO64::st(a.r64, it, rr);
-                if constexpr (std::is_same<T, __half>::value) {
+                if constexpr (kDemoteFromOdd<T>) {
                     float ro[R];
 #pragma unroll
                     for (int q = 0; q < R; ++q) ro[q] = __uint_as_float(float_bits_round_odd(rr[q]));
@@ -182,9 +182,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
             g[0] = l0;
             g[1] = l1;
         };
-        if constexpr (std::is_same<T, __half>::value) {
+        if constexpr (kDemoteFromOdd<T>) {
             // from the round-to-odd FP32 copy where that is exact, else from FP64
-            if (e >= -100 && e <= 126) d_pass(XDemoteOdd{a.r32, ldexpf(1.0f, -e)});
+            if (e >= -100 && e <= 126) d_pass(XDemoteOdd<T>{a.r32, ldexpf(1.0f, -e)});
             else d_pass(XDemote<T>{a.r64, ldexp(1.0, -e)});
         } else {
             d_pass(XDemote<T>{a.r64, ldexp(1.0, -e)});

@@ -495,7 +495,8 @@ gadi_status gadi_sylv_set_params(gadi_sylv *s, double alpha, double omega, gadi_
     if (!s) return GADI_ERR_INVALID_ARG;
     if (!(alpha > 0.0) || !std::isfinite(alpha)) return sfail(s, GADI_ERR_INVALID_ARG, "alpha must be positive");
     if (!(omega >= 0.0 && omega < 2.0)) return sfail(s, GADI_ERR_INVALID_ARG, "omega must lie in [0, 2)");
-    if (u_r < GADI_F64 || u_r > GADI_BF16) return sfail(s, GADI_ERR_INVALID_ARG, "unknown precision");
+    if (u_r < GADI_F64 || u_r > GADI_E4M3) return sfail(s, GADI_ERR_INVALID_ARG, "unknown precision");
+    if (u_r == GADI_E4M3) return sfail(s, GADI_ERR_UNSUPPORTED, "no FP8 inner precision for the Sylvester solver");
     s->alpha = alpha;
     s->omega = omega;
     s->u_r = u_r;

@@ -19,7 +19,7 @@ GADI_OK, GADI_ERR_INVALID_ARG, GADI_ERR_OUT_OF_MEMORY, GADI_ERR_CUDA = 0, 1, 2, 
 GADI_ERR_RANGE, GADI_ERR_NOT_CONVERGED, GADI_ERR_DIVERGED, GADI_ERR_TIMEOUT = 4, 5, 6, 7
 GADI_ERR_NO_MODEL, GADI_ERR_UNSUPPORTED = 8, 9
 GADI_SPLIT_HSS, GADI_SPLIT_USER = 0, 1
-GADI_F64, GADI_F32, GADI_F16, GADI_BF16 = 0, 1, 2, 3
+GADI_F64, GADI_F32, GADI_F16, GADI_BF16, GADI_E4M3 = 0, 1, 2, 3, 4
 GADI_STOP_ETA, GADI_STOP_RES = 0, 1
 GADI_KERNEL_AUTO, GADI_KERNEL_SPARSE, GADI_KERNEL_STENCIL = 0, 1, 2
 OP_A, OP_H, OP_S, OP_ST = 0, 1, 2, 3

@@ -455,6 +455,25 @@ def test_full_size_64cubed_workload_against_oracle():
     assert np.linalg.norm(x - p.x_exact) <= rn / lam + 1e-11
 
 
+def test_e4m3_inner_64cubed_reaches_fp64_floor():
+    """Cor. 1 at the bench's size: FP8 E4M3 inner storage (4 significant
+    bits, scaled like FP16) still drives eta to 1e-13 and the solution to the
+    FP64-inner one; the forward error obeys the same bound as FP16."""
+    p = P.workload("convdiff3d_64_b100")
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 3.0, 0.0, u_r=G.GADI_E4M3)
+        G.gadi_set_inner(h, 0.1, 500, 100000)
+        st, info, x = _solve(h, p, 1e-13)
+        assert st == G.GADI_OK, G.last_error(h)
+    finally:
+        G.gadi_destroy(h)
+    assert oracle.backward_error(p.A, p.b, x) <= 1e-13
+    lam = 3 * (2 - 2 * np.cos(np.pi / 65))
+    rn = np.linalg.norm(oracle.residual(p.A, p.b, x))
+    assert np.linalg.norm(x - p.x_exact) <= rn / lam + 1e-11
+
+
 def test_hbm_workload_192cubed_properties():
     """The bench's HBM-bound system (192^3, n = 7.1e6) at full size, in the
     launch configuration the bench times (automatic: 152 x 512): eta
@@ -627,7 +646,8 @@ def test_naive_fp16_loose_tolerance_matches_oracle():
 
 
 # ---------------------------------------------------------------------------
-# other inner precisions: FP32 and bfloat16 storage (precision variants)
+# other inner precisions: FP32, bfloat16 and FP8 E4M3 storage (precision
+# variants)
 # ---------------------------------------------------------------------------
 
 def _bf16_vector(n, seed):
@@ -635,32 +655,82 @@ def _bf16_vector(n, seed):
     return bits, (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
 
 
+def _e4m3_table():
+    """Value of each 8-bit E4M3 code from the format's layout (sign, 4
+    exponent bits with bias 7, 3 fraction bits, subnormals f 2^-9, the two
+    all-ones codes NaN)."""
+    t = np.empty(256)
+    for c in range(256):
+        s, e, f = (-1.0 if c & 0x80 else 1.0), (c >> 3) & 0xF, c & 7
+        if e == 0xF and f == 7:
+            t[c] = np.nan
+        elif e == 0:
+            t[c] = s * f * 2.0 ** -9
+        else:
+            t[c] = s * (1 + f / 8) * 2.0 ** (e - 7)
+    return t
+
+
+E4M3 = _e4m3_table()
+
+
+def _e4m3_vector(n, seed):
+    codes = oracle.to_e4m3_bits(P.random_vector(n, seed))
+    return codes, E4M3[codes]
+
+
+def _lp_vector(n, seed, u_r):
+    if u_r == G.GADI_BF16:
+        return _bf16_vector(n, seed)
+    if u_r == G.GADI_E4M3:
+        return _e4m3_vector(n, seed)
+    return None, P.random_vector(n, seed).astype(np.float32).astype(np.float64)
+
+
 def _lp_tensor(x, u_r, bits=None):
     if u_r == G.GADI_BF16:
         return torch.from_numpy(bits.view(np.int16).copy()).cuda().view(torch.bfloat16)
+    if u_r == G.GADI_E4M3:
+        return torch.from_numpy(bits.copy()).cuda()
     return _dev(x, torch.float32)
+
+
+def _lp_values(yd, u_r):
+    if u_r == G.GADI_E4M3:
+        return E4M3[yd.cpu().numpy()]
+    return yd.double().cpu().numpy()
+
+
+LP_CASES = [(G.GADI_F32, oracle.PREC_SINGLE), (G.GADI_BF16, oracle.PREC_BF16),
+            (G.GADI_E4M3, oracle.PREC_E4M3)]
 
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
 @pytest.mark.parametrize("kernel", [G.GADI_KERNEL_SPARSE, G.GADI_KERNEL_STENCIL])
-@pytest.mark.parametrize("u_r,prec", [(G.GADI_F32, oracle.PREC_SINGLE), (G.GADI_BF16, oracle.PREC_BF16)])
+@pytest.mark.parametrize("u_r,prec", LP_CASES)
 def test_apply_other_precisions_bit_exact(name, kernel, u_r, prec):
     p = PROBLEMS[name]()
     h = _handle(p)
     try:
         G.gadi_set_params(h, 0.37, 1.0, u_r=u_r)
         G.gadi_set_kernel(h, kernel)
+        if u_r == G.GADI_E4M3 and p.faces is not None:
+            # GRF face coefficients span more binades than FP8 holds after the
+            # scaling: entries below 2^-10 would vanish, and the solver refuses
+            bits, x = _lp_vector(p.n, 70, u_r)
+            xd = _lp_tensor(x, u_r, bits)
+            with pytest.raises(G.GadiError) as e:
+                G.gadi_apply(h, G.OP_H, xd, torch.empty_like(xd))
+            assert e.value.status == G.GADI_ERR_RANGE
+            return
         for which in (G.OP_H, G.OP_S, G.OP_ST):
-            if u_r == G.GADI_BF16:
-                bits, x = _bf16_vector(p.n, 70 + which)
-            else:
-                bits, x = None, P.random_vector(p.n, 70 + which).astype(np.float32).astype(np.float64)
+            bits, x = _lp_vector(p.n, 70 + which, u_r)
             want, sM, sN = oracle.lp_apply(p.A, 0.37, which, prec, x)
             xd = _lp_tensor(x, u_r, bits)
             yd = torch.empty_like(xd)
             G.gadi_apply(h, which, xd, yd)
             torch.cuda.synchronize()
-            got = yd.double().cpu().numpy()
+            got = _lp_values(yd, u_r)
             if kernel == G.GADI_KERNEL_STENCIL and p.faces is not None and u_r == G.GADI_F32 \
                     and which in (G.OP_S, G.OP_ST):
                 # the face stencil applies N as the constant c = beta h / 2 (see the FP64 case)
@@ -673,7 +743,7 @@ def test_apply_other_precisions_bit_exact(name, kernel, u_r, prec):
 
 
 @pytest.mark.parametrize("rows", [1, 4, 8])
-@pytest.mark.parametrize("u_r,prec", [(G.GADI_F32, oracle.PREC_SINGLE), (G.GADI_BF16, oracle.PREC_BF16)])
+@pytest.mark.parametrize("u_r,prec", LP_CASES)
 def test_apply_other_precisions_item_rows(rows, u_r, prec):
     p = ROWS_PROBLEMS["3d_16_b40"]()
     h = _handle(p)
@@ -682,30 +752,28 @@ def test_apply_other_precisions_item_rows(rows, u_r, prec):
         G.gadi_set_kernel(h, G.GADI_KERNEL_STENCIL)
         G.gadi_set_item_rows(h, rows)
         for which in (G.OP_H, G.OP_S, G.OP_ST):
-            if u_r == G.GADI_BF16:
-                bits, x = _bf16_vector(p.n, 80 + which)
-            else:
-                bits, x = None, P.random_vector(p.n, 80 + which).astype(np.float32).astype(np.float64)
+            bits, x = _lp_vector(p.n, 80 + which, u_r)
             want, _, _ = oracle.lp_apply(p.A, 2.0, which, prec, x)
             xd = _lp_tensor(x, u_r, bits)
             yd = torch.empty_like(xd)
             G.gadi_apply(h, which, xd, yd)
             torch.cuda.synchronize()
-            assert np.array_equal(yd.double().cpu().numpy(), want), (rows, which)
+            assert np.array_equal(_lp_values(yd, u_r), want), (rows, which)
     finally:
         G.gadi_destroy(h)
 
 
-@pytest.mark.parametrize("u_r,prec", [(G.GADI_F32, oracle.PREC_SINGLE), (G.GADI_BF16, oracle.PREC_BF16)])
+@pytest.mark.parametrize("u_r,prec", LP_CASES)
 @pytest.mark.parametrize("kernel", [G.GADI_KERNEL_SPARSE, G.GADI_KERNEL_STENCIL])
 def test_other_precision_solves_match_oracle(u_r, prec, kernel):
     p = PROBLEMS["3d_13_b100"]()
-    want, oinfo, _ = oracle.gadi_ir(p.A, p.b, 3.0, 1.0, tol=1e-13, eps_inner=1e-2, prec=prec, max_outer=5000)
+    eps = 0.1 if u_r == G.GADI_E4M3 else 1e-2      # FP8 inner solves stop at 0.1 by default
+    want, oinfo, _ = oracle.gadi_ir(p.A, p.b, 3.0, 1.0, tol=1e-13, eps_inner=eps, prec=prec, max_outer=5000)
     assert oinfo["status"] == oracle.OK
     h = _handle(p)
     try:
         G.gadi_set_params(h, 3.0, 1.0, u_r=u_r)
-        G.gadi_set_inner(h, 1e-2, 200, 5000)
+        G.gadi_set_inner(h, eps, 200, 5000)
         G.gadi_set_kernel(h, kernel)
         st, info, x = _solve(h, p, 1e-13)
         assert st == G.GADI_OK, G.last_error(h)

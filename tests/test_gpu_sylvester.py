@@ -94,6 +94,9 @@ def test_one_by_one_and_invalid_arguments():
         for alpha, omega in ((0.0, 1.0), (1.0, 2.0)):
             with pytest.raises(G.GadiError):
                 G.gadi_sylv_set_params(s, alpha, omega)
+        with pytest.raises(G.GadiError) as e:
+            G.gadi_sylv_set_params(s, 1.0, 1.0, G.GADI_E4M3)            # no FP8 Sylvester path
+        assert e.value.status == G.GADI_ERR_UNSUPPORTED
         with pytest.raises(G.GadiError):
             G.gadi_sylv_solve(s, np.ones((1, 1)), np.zeros((1, 1)))       # host arrays are rejected
     finally:
