@@ -200,21 +200,41 @@ def profiled_traffic(name, algorithmic):
     return round(float(fields["dram-bytes-per-launch"]) * algorithmic / float(fields["algorithmic-bytes-per-launch"]))
 
 
-def apply_bandwidth(G, torch, p, stencil, kernels, flush_l2, stream, reps=10):
-    """GB/s of one H' application per kernel variant: algorithmic bytes (x
-    read once, y written once, matrix bytes as stored per stored entry or per
-    node) over the median CUDA-event time, L2 flushed before each launch."""
+L2_BYTES = 129e6
+
+
+def apply_bandwidth(G, torch, p, stencil, kernels, flush_l2, stream, reps=10, precs=("fp16", "fp64")):
+    """GB/s of H' applications per kernel variant and inner precision, on
+    algorithmic bytes (x read once, y written once, matrix bytes as stored
+    per stored entry or per node):
+      GBps           one launch, L2 flushed before it (median CUDA-event time);
+      GBps_streamed  back-to-back launches over rotating (x, y) pairs whose
+                     footprint exceeds twice the L2, per-launch time from one
+                     event pair: the rate of a sweep kernel once launch
+                     latency overlaps the previous launch (None where the
+                     matrix arrays, read by every launch, fit in L2)."""
     t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
     h = G.gadi_create(t(p.A.row_ptr, torch.int32), t(p.A.col_idx, torch.int32), t(p.A.val),
                       stencil=stencil, stream=stream.cuda_stream)
     n, nnz = p.n, p.A.nnz
+    kinds = {"fp16": (G.GADI_F16, torch.float16, 2), "fp64": (G.GADI_F64, torch.float64, 8),
+             "fp8_e4m3": (G.GADI_E4M3, torch.uint8, 1)}
     out = {}
+
+    def vec(dt):
+        if dt == torch.uint8:
+            # E4M3 codes of moderate magnitude with random signs (no NaN codes)
+            return (torch.randint(0x20, 0x60, (n,), dtype=torch.uint8, device="cuda")
+                    | (torch.randint(0, 2, (n,), dtype=torch.uint8, device="cuda") << 7))
+        return torch.randn(n, device="cuda").to(dt)
+
     try:
         for kname, kk in kernels:
             G.gadi_set_kernel(h, kk)
-            for prec, u_r, dt, vs in (("fp16", G.GADI_F16, torch.float16, 2), ("fp64", G.GADI_F64, torch.float64, 8)):
+            for prec in precs:
+                u_r, dt, vs = kinds[prec]
                 G.gadi_set_params(h, 3.0, 0.0, u_r=u_r)
-                xi = torch.randn(n, device="cuda").to(dt)
+                xi = vec(dt)
                 yo = torch.empty_like(xi)
                 for _ in range(3):
                     G.gadi_apply(h, G.OP_H, xi, yo)
@@ -235,8 +255,29 @@ def apply_bandwidth(G, torch, p, stencil, kernels, flush_l2, stream, reps=10):
                     mat = 0
                 byts = 2 * n * vs + mat
                 med = statistics.median(ts)
-                out[f"{p.name}_{kname}_{prec}_H"] = {"GBps": round(byts / med / 1e9, 1), "bytes": byts,
-                                                     "us": round(med * 1e6, 2)}
+                key = f"{p.name}_{kname}_{prec}_H"
+                out[key] = {"GBps": round(byts / med / 1e9, 1), "bytes": byts, "us": round(med * 1e6, 2)}
+                if 0 < mat < 1.5 * L2_BYTES:
+                    # the matrix (or face) arrays would stay in L2 from one launch to the next
+                    out[key]["GBps_streamed"] = None
+                    continue
+                # streamed: rotating pairs so that no launch finds its vectors in L2
+                npairs = int(min(32, max(2, np.ceil(2 * L2_BYTES / (2 * n * vs)))))
+                xs = [vec(dt) for _ in range(npairs)]
+                ys = [torch.empty_like(xi) for _ in range(npairs)]
+                launches = max(20, 2 * npairs)
+                flush_l2()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for k in range(launches):
+                    G.gadi_apply(h, G.OP_H, xs[k % npairs], ys[k % npairs])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                per = e0.elapsed_time(e1) * 1e-3 / launches
+                del xs, ys
+                out[key].update({"GBps_streamed": round(byts / per / 1e9, 1), "us_streamed": round(per * 1e6, 2),
+                                 "streamed_pairs": npairs, "streamed_launches": launches})
     finally:
         G.gadi_destroy(h)
     return out
@@ -554,7 +595,8 @@ def run_gpu(args, rank, world):
         del p128
         p192 = P.make_problem(3, 192, 100.0, name="convdiff3d_192_b100")
         spmv.update(apply_bandwidth(G, torch, p192, (3, 192, 100.0, 0),
-                                    (("stencil", G.GADI_KERNEL_STENCIL),), flush_l2, stream))
+                                    (("stencil", G.GADI_KERNEL_STENCIL), ("sparse", G.GADI_KERNEL_SPARSE)),
+                                    flush_l2, stream, precs=("fp16", "fp8_e4m3", "fp64")))
         del p192
     G.gadi_set_kernel(h, kern)
     sylv = None
