@@ -651,7 +651,7 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
         // enough threads for one item each on every SM, between 128 and 1024
         const int64_t per_sm = (nitems + h->num_sms - 1) / h->num_sms;
         threads = 128;
-        while (threads < max_threads<Op>() && threads < per_sm) threads *= 2;
+        while (threads < max_threads<Op>() && threads < per_sm) threads = std::min(2 * threads, max_threads<Op>());
         if (nitems <= 16384) threads = max_threads<Op>();
     }
     if (threads > max_threads<Op>())
@@ -757,7 +757,8 @@ gadi_status run_apply(gadi_solver *h, int which, const void *x, void *y)
     // launch shape: gadi_set_launch's when given, else one item per thread
     const int threads = h->threads ? h->threads : kSetupThreads;
     const unsigned blocks = h->blocks ? (unsigned)h->blocks : grid_for(nitems, threads);
-    gadi_apply_kernel<Op, T><<<blocks, threads, 0, h->stream>>>(op, nitems, which, x, y);
+    if constexpr (Op::R == 8) gadi_apply_kernel_wide<Op, T><<<blocks, threads, 0, h->stream>>>(op, nitems, which, x, y);
+    else gadi_apply_kernel<Op, T><<<blocks, threads, 0, h->stream>>>(op, nitems, which, x, y);
     CK(cudaGetLastError());
     return GADI_OK;
 }

@@ -20,6 +20,8 @@ enum : int {
     kErrNotConverged = 5, kErrDiverged = 6, kErrTimeout = 7
 };
 
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
 // ---------------------------------------------------------------------------
 // Precision traits. T is the storage type of the inner vectors and matrix
 // values; Acc the arithmetic type (FP32 for FP16 storage, FP64 otherwise).

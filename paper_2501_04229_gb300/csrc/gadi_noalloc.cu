@@ -162,7 +162,7 @@ gadi_status launch(int dev, int num_sms, cudaStream_t stream, unsigned char *bas
     int threads = 128;
     {
         const int64_t per_sm = (nitems + num_sms - 1) / num_sms;
-        while (threads < max_threads<Op>() && threads < per_sm) threads *= 2;
+        while (threads < max_threads<Op>() && threads < per_sm) threads = std::min(2 * threads, max_threads<Op>());
         if (nitems <= 16384) threads = max_threads<Op>();
     }
     int per_sm = 0;

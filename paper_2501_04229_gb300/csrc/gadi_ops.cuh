@@ -523,54 +523,79 @@ struct StencilOp {
     // ---- R-row items (R = 4 or 8) ----------------------------------------------
     // Items of R: neighbours along y and z are whole aligned chunks; along x
     // they are the item's own values shifted by one, with the two ends from
-    // one().
+    // one(). Every neighbour value of an item is read before its first term
+    // is formed: a neighbour outside the grid reads the item's own chunk (a
+    // valid address) and its term is left out afterwards, so the item's
+    // loads issue back to back and a pass waits for memory once per item
+    // rather than once per neighbour. Terms and their order are unchanged.
+    // The FP64 inner path (bound by the FP64 rate, and short of registers
+    // for eight FP64 chunks) loads each neighbour where its term is formed.
+    static constexpr bool kHoist = !std::is_same<T, double>::value;
     template <class F>
     __device__ __forceinline__ void rowsA(int64_t item, const F &f, double (&out)[R]) const
     {
         if constexpr (R == 1) {
             out[0] = rowA1(item, f);
         } else {
+            constexpr int NB = DIM - 1;
             const int64_t i0 = item * R;
             unsigned cd[3];
             coords(i0, cd);
             const unsigned last = (unsigned)N - 1;
             const bool face = AD != nullptr;
-            double c[R], acc[R], t[R], cf[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] = 0.0;
+            bool hl[NB], hu[NB];
+            double c[R], acc[R], cf[R], tl[NB][R], tu[NB][R];
             f.template many<R>(i0, c);
 #pragma unroll
+            for (int d = 1; d < DIM; ++d) {
+                hl[d - 1] = cd[d] > 0;
+                hu[d - 1] = cd[d] < last;
+                if constexpr (kHoist) {
+                    f.template many<R>(hl[d - 1] ? i0 - stride(d) : i0, tl[d - 1]);
+                    f.template many<R>(hu[d - 1] ? i0 + stride(d) : i0, tu[d - 1]);
+                }
+            }
+            const bool hxm = cd[0] > 0, hxp = cd[0] + R <= last;
+            double xm = 0.0, xp = 0.0;
+            if constexpr (kHoist) {
+                xm = f.one(hxm ? i0 - 1 : i0);
+                xp = f.one(hxp ? i0 + R : i0);
+            } else {
+                if (hxm) xm = f.one(i0 - 1);
+                if (hxp) xp = f.one(i0 + R);
+            }
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] = 0.0;
+#pragma unroll
             for (int d = DIM - 1; d >= 1; --d)
-                if (cd[d] > 0) {
-                    f.template many<R>(i0 - stride(d), t);
+                if (hl[d - 1]) {
+                    if constexpr (!kHoist) f.template many<R>(i0 - stride(d), tl[d - 1]);
                     if (face) ldv<R>(AL[d], i0, cf);
 #pragma unroll
-                    for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_lo, t[k], acc[k]);
+                    for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_lo, tl[d - 1][k], acc[k]);
                 }
             {   // x lower
-                const double xm = cd[0] > 0 ? f.one(i0 - 1) : 0.0;
                 if (face) ldv<R>(AL[0], i0, cf);
 #pragma unroll
                 for (int k = 0; k < R; ++k)
-                    if (k > 0 || cd[0] > 0) acc[k] = __fma_rn(face ? cf[k] : a_lo, k ? c[k - 1] : xm, acc[k]);
+                    if (k > 0 || hxm) acc[k] = __fma_rn(face ? cf[k] : a_lo, k ? c[k - 1] : xm, acc[k]);
             }
             if (face) ldv<R>(AD, i0, cf);
 #pragma unroll
             for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_diag, c[k], acc[k]);
             {   // x upper
-                const double xp = cd[0] + R <= last ? f.one(i0 + R) : 0.0;
                 if (face) ldv<R>(AU[0], i0, cf);
 #pragma unroll
                 for (int k = 0; k < R; ++k)
-                    if (k < R - 1 || cd[0] + R <= last) acc[k] = __fma_rn(face ? cf[k] : a_hi, k < R - 1 ? c[k + 1] : xp, acc[k]);
+                    if (k < R - 1 || hxp) acc[k] = __fma_rn(face ? cf[k] : a_hi, k < R - 1 ? c[k + 1] : xp, acc[k]);
             }
 #pragma unroll
             for (int d = 1; d < DIM; ++d)
-                if (cd[d] < last) {
-                    f.template many<R>(i0 + stride(d), t);
+                if (hu[d - 1]) {
+                    if constexpr (!kHoist) f.template many<R>(i0 + stride(d), tu[d - 1]);
                     if (face) ldv<R>(AU[d], i0, cf);
 #pragma unroll
-                    for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_hi, t[k], acc[k]);
+                    for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_hi, tu[d - 1][k], acc[k]);
                 }
 #pragma unroll
             for (int k = 0; k < R; ++k) out[k] = acc[k];
@@ -588,34 +613,54 @@ struct StencilOp {
             // x neighbours are the item's own values shifted by one, with a
             // zero term (value 0, so the sum keeps its value) where a row has
             // no neighbour
+            constexpr int NB = DIM - 1;
             const int64_t i0 = item * R;
             unsigned cd[3];
             coords(i0, cd);
             const unsigned last = (unsigned)N - 1;
-            Acc c[R], acc[R], t[R], cf[R], sh[R];
+            bool hl[NB], hu[NB];
+            Acc c[R], acc[R], cf[R], sh[R], tl[NB][R], tu[NB][R];
             f.template many<R>(i0, c);
+#pragma unroll
+            for (int d = 1; d < DIM; ++d) {
+                hl[d - 1] = cd[d] > 0;
+                hu[d - 1] = cd[d] < last;
+                if constexpr (kHoist) {
+                    f.template many<R>(hl[d - 1] ? i0 - stride(d) : i0, tl[d - 1]);
+                    f.template many<R>(hu[d - 1] ? i0 + stride(d) : i0, tu[d - 1]);
+                }
+            }
+            const bool hxm = cd[0] > 0, hxp = cd[0] + R <= last;
+            Acc xm = Acc(0), xp = Acc(0);
+            if constexpr (kHoist) {
+                const Acc xm0 = f.one(hxm ? i0 - 1 : i0), xp0 = f.one(hxp ? i0 + R : i0);
+                xm = hxm ? xm0 : Acc(0);
+                xp = hxp ? xp0 : Acc(0);
+            } else {
+                if (hxm) xm = f.one(i0 - 1);
+                if (hxp) xp = f.one(i0 + R);
+            }
             if (which == kOpH) {
                 const bool face = HD != nullptr;
                 P::mul_s(acc, sigH, c);
 #pragma unroll
                 for (int d = DIM - 1; d >= 1; --d)
-                    if (cd[d] > 0) {
-                        f.template many<R>(i0 - stride(d), t);
+                    if (hl[d - 1]) {
+                        if constexpr (!kHoist) f.template many<R>(i0 - stride(d), tl[d - 1]);
                         if (face) {
                             ldv<R>(HK[d], i0 - stride(d), cf);
-                            P::madd_v(acc, acc, cf, t);
+                            P::madd_v(acc, acc, cf, tl[d - 1]);
                         } else {
-                            P::madd_s(acc, acc, h_off, t);
+                            P::madd_s(acc, acc, h_off, tl[d - 1]);
                         }
                     }
                 {   // x lower: coupling of node i with i-1 is HK[0][i-1]
-                    const Acc xm = cd[0] > 0 ? f.one(i0 - 1) : Acc(0);
 #pragma unroll
                     for (int k = 0; k < R; ++k) sh[k] = k ? c[k - 1] : xm;
                     if (face) {
                         Acc cs[R];
                         ldv<R>(HK[0], i0, cf);
-                        cs[0] = cd[0] > 0 ? P::ld(HK[0][i0 - 1]) : Acc(0);
+                        cs[0] = hxm ? P::ld(HK[0][i0 - 1]) : Acc(0);
 #pragma unroll
                         for (int k = 1; k < R; ++k) cs[k] = cf[k - 1];
                         P::madd_v(acc, acc, cs, sh);
@@ -631,7 +676,6 @@ struct StencilOp {
                     P::madd_s(acc, acc, h_diag, c);
                 }
                 {   // x upper: coupling HK[0][i]
-                    const Acc xp = cd[0] + R <= last ? f.one(i0 + R) : Acc(0);
 #pragma unroll
                     for (int k = 0; k < R; ++k) sh[k] = k < R - 1 ? c[k + 1] : xp;
                     if (face) P::madd_v(acc, acc, cf, sh);
@@ -639,13 +683,13 @@ struct StencilOp {
                 }
 #pragma unroll
                 for (int d = 1; d < DIM; ++d)
-                    if (cd[d] < last) {
-                        f.template many<R>(i0 + stride(d), t);
+                    if (hu[d - 1]) {
+                        if constexpr (!kHoist) f.template many<R>(i0 + stride(d), tu[d - 1]);
                         if (face) {
                             ldv<R>(HK[d], i0, cf);
-                            P::madd_v(acc, acc, cf, t);
+                            P::madd_v(acc, acc, cf, tu[d - 1]);
                         } else {
-                            P::madd_s(acc, acc, h_off, t);
+                            P::madd_s(acc, acc, h_off, tu[d - 1]);
                         }
                     }
             } else {
@@ -653,28 +697,26 @@ struct StencilOp {
                 P::mul_s(acc, sigS, c);
 #pragma unroll
                 for (int d = DIM - 1; d >= 1; --d)
-                    if (cd[d] > 0) {
-                        f.template many<R>(i0 - stride(d), t);
-                        P::madd_s(acc, acc, lo, t);
+                    if (hl[d - 1]) {
+                        if constexpr (!kHoist) f.template many<R>(i0 - stride(d), tl[d - 1]);
+                        P::madd_s(acc, acc, lo, tl[d - 1]);
                     }
                 {
-                    const Acc xm = cd[0] > 0 ? f.one(i0 - 1) : Acc(0);
 #pragma unroll
                     for (int k = 0; k < R; ++k) sh[k] = k ? c[k - 1] : xm;
                     P::madd_s(acc, acc, lo, sh);
                 }
                 if (s_diag != Acc(0)) P::madd_s(acc, acc, s_diag, c);
                 {
-                    const Acc xp = cd[0] + R <= last ? f.one(i0 + R) : Acc(0);
 #pragma unroll
                     for (int k = 0; k < R; ++k) sh[k] = k < R - 1 ? c[k + 1] : xp;
                     P::madd_s(acc, acc, -lo, sh);
                 }
 #pragma unroll
                 for (int d = 1; d < DIM; ++d)
-                    if (cd[d] < last) {
-                        f.template many<R>(i0 + stride(d), t);
-                        P::madd_s(acc, acc, -lo, t);
+                    if (hu[d - 1]) {
+                        if constexpr (!kHoist) f.template many<R>(i0 + stride(d), tu[d - 1]);
+                        P::madd_s(acc, acc, -lo, tu[d - 1]);
                     }
             }
 #pragma unroll

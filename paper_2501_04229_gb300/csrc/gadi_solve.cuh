@@ -59,10 +59,11 @@ struct SolveArgs {
 // status of a solve stopped by race_bound (reported as not converged)
 constexpr int kRacedOut = 100;
 
-// launch bound: 1024 threads for one-row items, 512 for 4- and 8-row items
-// (whose per-thread state is larger)
+// launch bound: 1024 threads for one-row items, 512 for 4-row and 384 for
+// 8-row items (whose per-thread state is larger: an item holds all its
+// neighbour chunks at once)
 template <class Op>
-__host__ __device__ constexpr int max_threads() { return Op::R > 1 ? 512 : 1024; }
+__host__ __device__ constexpr int max_threads() { return Op::R > 4 ? 384 : (Op::R > 1 ? 512 : 1024); }
 
 // The solve, run by a team of threads: the whole grid (ex.block_only false,
 // t0/nt the global thread index and count) or one block (ex.block_only true,
@@ -95,7 +96,12 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
         // ---- R: outer residual in FP64 -----------------------------------------
         double vR[3] = {0.0, 0.0, 0.0};
         {
-            double lmax = 0.0, lsum = 0.0, xmax = 0.0;
+            // the maxima of |r| and |x| as integer maxima of the magnitudes' bit
+            // patterns (same value for finite inputs; FP64 compares issue at
+            // the FP64 rate on this GPU, integer ones at the integer rate)
+            double lsum = 0.0;
+            uint64_t lmax = 0, xmax = 0;
+            constexpr uint64_t kMag = 0x7FFFFFFFFFFFFFFFull;
             const XLoad64 fx{xcur};
             for (int64_t it = t0; it < items; it += nt) {
                 double ax[R], bb[R], xx[R], rr[R];
@@ -105,9 +111,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
                     rr[q] = __dsub_rn(bb[q], ax[q]);
-                    lmax = fmax(lmax, fabs(rr[q]));
+                    lmax = umax64(lmax, bits_of(rr[q]) & kMag);
                     lsum = __fma_rn(rr[q], rr[q], lsum);
-                    xmax = fmax(xmax, fabs(xx[q]));
+                    xmax = umax64(xmax, bits_of(xx[q]) & kMag);
                 }
                 IO64::st(a.r64, it, rr);
                 if constexpr (kDemoteFromOdd<T>) {
@@ -119,8 +125,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
                 }
             }
             vR[0] = lsum;
-            vR[1] = lmax;
-            vR[2] = xmax;
+            vR[1] = double_of(lmax);
+            vR[2] = double_of(xmax);
         }
         {
             const int opsR[3] = {kSum, kMax, kMax};
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(max_threads<Op>(), 1) gadi_solve_kernel(const 
 
 // One operator application y = K x (kernel-level tests, bandwidth runs).
 template <class Op, class T>
-__global__ void gadi_apply_kernel(const Op op, int64_t nitems, int which, const void *xv, void *yv)
+__device__ __forceinline__ void apply_body(const Op &op, int64_t nitems, int which, const void *xv, void *yv)
 {
     using P = Prec<T>;
     using Acc = typename P::Acc;
@@ -453,6 +459,21 @@ __global__ void gadi_apply_kernel(const Op op, int64_t nitems, int which, const 
         op.rows(which, it, f, o);
         ItemIO<T, R>::st((T *)yv, it, o);
     }
+}
+
+template <class Op, class T>
+__global__ void gadi_apply_kernel(const Op op, int64_t nitems, int which, const void *xv, void *yv)
+{
+    apply_body<Op, T>(op, nitems, which, xv, yv);
+}
+
+// The same for 8-row stencil items, which hold all their neighbour chunks
+// at once: at most 128 registers, so that two 256-thread blocks share an SM.
+template <class Op, class T>
+__global__ void __maxnreg__(128) gadi_apply_kernel_wide(const Op op, int64_t nitems, int which, const void *xv,
+                                                        void *yv)
+{
+    apply_body<Op, T>(op, nitems, which, xv, yv);
 }
 
 }  // namespace gadi
