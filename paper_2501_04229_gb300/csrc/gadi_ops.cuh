@@ -373,13 +373,37 @@ struct EllOp {
     const T *__restrict__ nt;         // 2^-sN N^T, or null when N^T = -N
     Acc sigH, sigS;                   // 2^-sM alpha, 2^-sN alpha
 
+    // the column indices of a row of the common width 8 (5- and 7-point
+    // rows), two 16-byte loads
+    __device__ __forceinline__ void cols8(const int *c, int (&cc)[8]) const
+    {
+        const int4 c0 = __ldg(reinterpret_cast<const int4 *>(c));
+        const int4 c1 = __ldg(reinterpret_cast<const int4 *>(c) + 1);
+        cc[0] = c0.x; cc[1] = c0.y; cc[2] = c0.z; cc[3] = c0.w;
+        cc[4] = c1.x; cc[5] = c1.y; cc[6] = c1.z; cc[7] = c1.w;
+    }
+
+    // Rows of width 8 read their columns and values with vector loads and
+    // issue all eight gathers before the first product; the products are
+    // summed in the same (ascending column) order as for any other width.
     template <class F>
     __device__ __forceinline__ void rowsA(int64_t i, const F &f, double (&out)[1]) const
     {
         const int *c = col + i * W;
         const double *v = a64 + i * W;
         double acc = 0.0;
-        for (int k = 0; k < W; ++k) acc = __fma_rn(__ldg(v + k), f.one(__ldg(c + k)), acc);
+        if (W == 8) {
+            int cc[8];
+            double vv[8], xv[8];
+            cols8(c, cc);
+            ldv<8>(v, 0, vv);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) xv[k] = f.one(cc[k]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc = __fma_rn(vv[k], xv[k], acc);
+        } else {
+            for (int k = 0; k < W; ++k) acc = __fma_rn(__ldg(v + k), f.one(__ldg(c + k)), acc);
+        }
         out[0] = acc;
     }
 
@@ -396,7 +420,18 @@ struct EllOp {
         else { v = nv; sig = sigS; sgn = Acc(-1); }
         v += i * W;
         Acc acc = P::mul(sig, f.one(i));
-        for (int k = 0; k < W; ++k) acc = P::madd(acc, sgn * P::ld(v[k]), f.one(__ldg(c + k)));
+        if (W == 8) {
+            int cc[8];
+            Acc vv[8], xv[8];
+            cols8(c, cc);
+            ldv<8>(v, 0, vv);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) xv[k] = f.one(cc[k]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc = P::madd(acc, sgn * vv[k], xv[k]);
+        } else {
+            for (int k = 0; k < W; ++k) acc = P::madd(acc, sgn * P::ld(v[k]), f.one(__ldg(c + k)));
+        }
         out[0] = acc;
     }
 };
