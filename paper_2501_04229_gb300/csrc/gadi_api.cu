@@ -754,6 +754,23 @@ gadi_status run_apply(gadi_solver *h, int which, const void *x, void *y)
     if constexpr (std::is_same<Op, EllOp<T>>::value) op = make_ell<T>(h);
     else op = make_stencil<T, Op::kDim, Op::R>(h);
     const int64_t nitems = h->n / Op::R;
+    if constexpr (std::is_same<Op, StencilOp<__half, 3, 8>>::value) {
+        // constant-coefficient FP16 stencil without a set launch shape: the
+        // z-marching kernel, with segments of at least 4 planes and about
+        // two 256-thread blocks per SM in all
+        if (!h->threads && !h->blocks && op.HD == nullptr && which != kOpA) {
+            const int64_t lines = (int64_t)(op.N / 8) * op.N;
+            const int64_t want = (int64_t)2 * 256 * h->num_sms;
+            const int64_t nzs = std::max<int64_t>(1, std::min<int64_t>(op.N / 4, want / lines));
+            const int zlen = (int)((op.N + nzs - 1) / nzs);
+            const int64_t segs = (op.N + zlen - 1) / zlen;
+            const unsigned blocks = (unsigned)((lines * segs + 255) / 256);
+            gadi_apply_zmarch_kernel<Op><<<blocks, 256, 0, h->stream>>>(op, which, zlen, (const __half *)x,
+                                                                        (__half *)y);
+            CK(cudaGetLastError());
+            return GADI_OK;
+        }
+    }
     // launch shape: gadi_set_launch's when given, else one item per thread
     const int threads = h->threads ? h->threads : kSetupThreads;
     const unsigned blocks = h->blocks ? (unsigned)h->blocks : grid_for(nitems, threads);

@@ -476,4 +476,115 @@ __global__ void __maxnreg__(128) gadi_apply_kernel_wide(const Op op, int64_t nit
     apply_body<Op, T>(op, nitems, which, xv, yv);
 }
 
+// Operator application for the constant-coefficient 3D stencil with FP16
+// vectors and 8-row items, marching along z: a thread takes the 8-row chunk
+// of one x-line at (x0, y) for a segment of zlen consecutive planes. The
+// chunks of planes z-1, z and z+1 stay in registers from one plane to the
+// next, so a plane costs one new 16-byte read (the chunk three planes
+// ahead, in flight while the thread works on the current plane); the y
+// neighbours and the x ends of the next plane are read one plane ahead.
+// Each row is formed with the terms of StencilOp::rows in the same order,
+// so the result is bit for bit that of gadi_apply_kernel.
+__device__ __forceinline__ void half8_to_float(const uint4 &u, float (&o)[8])
+{
+    const __half2 *h = reinterpret_cast<const __half2 *>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 f = __half22float2(h[k]);
+        o[2 * k] = f.x;
+        o[2 * k + 1] = f.y;
+    }
+}
+
+template <class Op>
+__global__ void __launch_bounds__(256, 2) gadi_apply_zmarch_kernel(const Op op, int which, int zlen,
+                                                                    const __half *x, __half *y)
+{
+    static_assert(Op::kDim == 3 && Op::R == 8, "3D stencil with 8-row items");
+    using P = Prec<__half>;
+    constexpr int R = 8;
+    const int N = op.N;
+    const int nx8 = N / R;
+    const int64_t NN = (int64_t)N * N;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cx = (int)(g % nx8);
+    const int64_t t = g / nx8;
+    const int yy = (int)(t % N);
+    const int64_t seg = t / N;
+    if (seg * zlen >= N) return;
+    const int z0 = (int)(seg * zlen);
+    const int z1 = min(N, z0 + zlen);
+    const int last = N - 1;
+    const int64_t base = (int64_t)cx * R + (int64_t)yy * N;   // row of (x0, y, z = 0)
+    const bool hly = yy > 0, huy = yy < last;
+    const bool hxm = cx > 0, hxp = cx * R + R <= last;
+    // neighbour offsets, clamped to the item itself where the grid ends
+    const int64_t oyl = hly ? -(int64_t)N : 0, oyu = huy ? (int64_t)N : 0;
+    const int64_t oxm = hxm ? -1 : 0, oxp = hxp ? R : 0;
+    auto chunk = [&](int z, int64_t off) { return *reinterpret_cast<const uint4 *>(x + base + off + (int64_t)z * NN); };
+
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    uint4 rm = z0 > 0 ? chunk(z0 - 1, 0) : zero4;              // plane z - 1
+    uint4 r0 = chunk(z0, 0);                                     // plane z
+    uint4 r1 = chunk(min(z0 + 1, last), 0);                      // plane z + 1
+    uint4 r2 = chunk(min(z0 + 2, min(z1, last)), 0);             // plane z + 2
+    uint4 ryl = chunk(z0, oyl), ryu = chunk(z0, oyu);            // y neighbours of plane z
+    __half hxl = x[base + oxm + (int64_t)z0 * NN], hxu = x[base + oxp + (int64_t)z0 * NN];
+    for (int z = z0; z < z1; ++z) {
+        // reads for later planes first: the chunk three planes ahead (never
+        // beyond the plane after the segment), the next plane's y and x reads
+        const uint4 r3 = chunk(min(z + 3, min(z1, last)), 0);
+        const int zq = min(z + 1, z1 - 1);
+        const uint4 nyl = chunk(zq, oyl), nyu = chunk(zq, oyu);
+        const __half nxl = x[base + oxm + (int64_t)zq * NN], nxu = x[base + oxp + (int64_t)zq * NN];
+
+        float c[R], zl[R], zu[R], yl[R], yu[R], acc[R], sh[R];
+        half8_to_float(rm, zl);
+        half8_to_float(r0, c);
+        half8_to_float(r1, zu);
+        half8_to_float(ryl, yl);
+        half8_to_float(ryu, yu);
+        const float xm = hxm ? P::ld(hxl) : 0.0f, xp = hxp ? P::ld(hxu) : 0.0f;
+        const bool hlz = z > 0, huz = z < last;
+        if (which == kOpH) {
+            P::mul_s(acc, op.sigH, c);
+            if (hlz) P::madd_s(acc, acc, op.h_off, zl);
+            if (hly) P::madd_s(acc, acc, op.h_off, yl);
+#pragma unroll
+            for (int k = 0; k < R; ++k) sh[k] = k ? c[k - 1] : xm;
+            P::madd_s(acc, acc, op.h_off, sh);
+            P::madd_s(acc, acc, op.h_diag, c);
+#pragma unroll
+            for (int k = 0; k < R; ++k) sh[k] = k < R - 1 ? c[k + 1] : xp;
+            P::madd_s(acc, acc, op.h_off, sh);
+            if (huy) P::madd_s(acc, acc, op.h_off, yu);
+            if (huz) P::madd_s(acc, acc, op.h_off, zu);
+        } else {
+            const float lo = which == kOpS ? -op.s_c : op.s_c;
+            P::mul_s(acc, op.sigS, c);
+            if (hlz) P::madd_s(acc, acc, lo, zl);
+            if (hly) P::madd_s(acc, acc, lo, yl);
+#pragma unroll
+            for (int k = 0; k < R; ++k) sh[k] = k ? c[k - 1] : xm;
+            P::madd_s(acc, acc, lo, sh);
+            if (op.s_diag != 0.0f) P::madd_s(acc, acc, op.s_diag, c);
+#pragma unroll
+            for (int k = 0; k < R; ++k) sh[k] = k < R - 1 ? c[k + 1] : xp;
+            P::madd_s(acc, acc, -lo, sh);
+            if (huy) P::madd_s(acc, acc, -lo, yu);
+            if (huz) P::madd_s(acc, acc, -lo, zu);
+        }
+        ItemIO<__half, R>::st(y, (base + (int64_t)z * NN) / R, acc);
+
+        rm = r0;
+        r0 = r1;
+        r1 = r2;
+        r2 = r3;
+        ryl = nyl;
+        ryu = nyu;
+        hxl = nxl;
+        hxu = nxu;
+    }
+}
+
 }  // namespace gadi

@@ -144,6 +144,36 @@ def test_apply_item_rows_bit_exact(name, rows, u_r):
         G.gadi_destroy(h)
 
 
+@pytest.mark.parametrize("N", [24, 48, 96])
+def test_apply_zmarch_bit_exact(N):
+    """The z-marching FP16 stencil application (8-row items, a segment of z
+    planes per thread, chunks carried from plane to plane in registers)
+    gives the oracle's application bit for bit, and the same bits as the
+    one-item-per-thread kernel that a set launch shape selects; N = 24, 48,
+    96 give 6, 12 and 24 segments per z-line and several blocks."""
+    p = P.make_problem(3, N, 60.0)
+    h = _handle(p)
+    try:
+        G.gadi_set_params(h, 0.37, 1.0, u_r=G.GADI_F16)
+        G.gadi_set_kernel(h, G.GADI_KERNEL_STENCIL)
+        G.gadi_set_item_rows(h, 8)
+        for which in (G.OP_H, G.OP_S, G.OP_ST):
+            x = _half_vector(p.n, 70 + which)
+            want, _, _ = oracle.lp_apply(p.A, 0.37, which, oracle.PREC_HALF, x)
+            xd = _dev(x, torch.float16)
+            y1 = torch.empty_like(xd)
+            y2 = torch.empty_like(xd)
+            G.gadi_set_launch(h, 0, 0)
+            G.gadi_apply(h, which, xd, y1)
+            G.gadi_set_launch(h, 0, 256)
+            G.gadi_apply(h, which, xd, y2)
+            torch.cuda.synchronize()
+            assert np.array_equal(y1.double().cpu().numpy(), want), which
+            assert torch.equal(y1, y2), which
+    finally:
+        G.gadi_destroy(h)
+
+
 def test_apply_user_split_bit_exact():
     p = P.make_problem(3, 9, 30.0)
     m_hss, _ = oracle.hss_split(p.A)
@@ -486,6 +516,19 @@ def test_hbm_workload_192cubed_properties():
         G.gadi_set_inner(h, 0.1, 500, 100000)
         st, info, x = _solve(h, p, 1e-13)
         assert st == G.GADI_OK and info["grid_blocks"] * info["block_threads"] >= 152 * 256
+        # the bench's operator application at this size (z-marching kernel,
+        # 12-plane segments) against the one-item-per-thread kernel
+        xh = torch.randn(p.n, device="cuda").half()
+        for which in (G.OP_H, G.OP_S, G.OP_ST):
+            y1 = torch.empty_like(xh)
+            y2 = torch.empty_like(xh)
+            G.gadi_set_launch(h, 0, 0)
+            G.gadi_apply(h, which, xh, y1)
+            G.gadi_set_launch(h, 0, 256)
+            G.gadi_apply(h, which, xh, y2)
+            torch.cuda.synchronize()
+            assert torch.equal(y1, y2), which
+        G.gadi_set_launch(h, 0, 0)
     finally:
         G.gadi_destroy(h)
     assert oracle.backward_error(p.A, p.b, x) <= 1e-13
