@@ -469,12 +469,9 @@ def sylvester_case(G, torch, m=1024, n=1024, r=0.1, alpha=0.05, omega=1.0):
     """GADI-AB for the Sylvester equation of §4.3 (A = B = M + 2 r N + 100/(n+1)^2 I,
     m = n = 1024, X* random, C = A X* + X* B): time to eta <= 1e-13 with FP16
     and FP64 inner solves on the GPU (one warm-up solve each first)."""
-    import oracle
-    a = oracle.sylvester_matrices(m, r)
-    b = oracle.sylvester_matrices(n, r)
-    Xs = np.random.default_rng(0).standard_normal((m, n))
-    A, B = oracle.tri_dense(*a), oracle.tri_dense(*b)
-    Cm = torch.from_numpy(A @ Xs + Xs @ B).cuda()
+    from paper_2501_04229_gb300 import problems as P
+    a, b, Xs, Cm = P.sylvester_problem(m, n, r, seed=0)
+    Cm = torch.from_numpy(Cm).cuda()
     out = {"m": m, "n": n, "r": r, "alpha": alpha, "omega": omega}
     s = G.gadi_sylv_create(a, b)
     try:

@@ -113,7 +113,9 @@ typedef struct {
     int64_t spmv_count;         /* operator applications in the solve (A, H, S, S^T) */
     double eta_inf;             /* backward error of the returned x */
     double res_rel;             /* RES of the returned x */
-    double t_solve_s;           /* device time of the solve (CUDA events) */
+    double t_solve_s;           /* device time of the solve (CUDA events; host wall time of
+                                   launch + synchronisation for gadi_solve_stencil_noalloc,
+                                   which creates no events) */
     int32_t scale_exp_M;        /* FP16 scale exponent of H (H stored as 2^-s H) */
     int32_t scale_exp_N;        /* FP16 scale exponent of S */
     int32_t kernel;             /* gadi_kernel actually used */
@@ -122,9 +124,13 @@ typedef struct {
     int32_t reserved;
 } gadi_info;
 
-/* Create a solver for A (copied to the device). split: GADI_SPLIT_HSS, or
+/* Create a solver for A (copied to the device): the problem statement of
+ * §1.2 (A x = b, A nonsingular, A = M + N) and Algorithm 1's inputs (A and
+ * its splitting). split: GADI_SPLIT_HSS, the Hermitian/skew-Hermitian
+ * splitting §4.1 uses (M = (A + A^T)/2, N = (A - A^T)/2), or
  * GADI_SPLIT_USER with M_user on A's exact pattern (same row_ptr/col_idx,
- * same on_device flag) and N = A - M; M must be symmetric for the CG on
+ * same on_device flag) and N = A - M (eq. (gadi) admits any splitting; Thm
+ * 1 states when it converges); M must be symmetric for the CG on
  * H = aI + M to apply. structure: optional stencil descriptor (see above).
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
  * Errors: INVALID_ARG (n < 1, bad pattern, pattern not symmetric, unsorted
@@ -151,7 +157,9 @@ GADI_API gadi_status gadi_set_params(gadi_solver *h, double alpha, double omega,
 
 /* Inner relative tolerance eps (0 < eps < 1): each inner solve stops when
  * ||rhs - K v||_2 <= eps ||rhs||_2, or after max_inner iterations (>= 1).
- * max_outer (>= 0) caps the refinement steps. Defaults: eps 1e-2 (FP32,
+ * This is Algorithm 1's inner tolerance on steps 2 and 3 ("tol <= eps
+ * ||r^(0)||_2"), read as relative to the current inner right-hand side.
+ * max_outer (>= 0) caps the refinement steps (Algorithm 1's outer loop). Defaults: eps 1e-2 (FP32,
  * FP16 and bfloat16 inner precision) / 0.1 (FP8 E4M3) / 1e-10 (FP64 inner),
  * max_inner 200, max_outer 100000. */
 GADI_API gadi_status gadi_set_inner(gadi_solver *h, double eps_inner, int32_t max_inner, int32_t max_outer);
@@ -201,7 +209,13 @@ GADI_API gadi_status gadi_set_wait_limit(gadi_solver *h, double milliseconds);
  * fault and no hang: the wait is bounded by gadi_set_wait_limit. */
 GADI_API gadi_status gadi_debug_force_timeout(gadi_solver *h, int32_t on);
 
-/* Solve A x = b. b (n FP64) and x (n FP64; in: x0, out: the result) are
+/* Solve A x = b by Algorithm 1 (GADI-IR): repeat r = b - A x in u_f
+ * (step 1), the inner solves with aI + M and aI + N in u_r (steps 2 and 3),
+ * x += the correction in u (step 4), until the stopping test holds: eta_inf
+ * <= tol (the normwise backward error, Thm 3's measure with infinity norms)
+ * or RES <= tol (§4.1's relative residual), as gadi_set_stop selects. With
+ * u_r = GADI_F64 this is eq. (gadi)'s plain FP64 GADI. b (n FP64) and x (n
+ * FP64; in: x0, Algorithm 1's starting vector, out: the result) are
  * both host or both device pointers. Host buffers are copied to and from
  * library-owned device memory inside the call. Returns after the result is
  * in x (the stream is synchronised). tol > 0 applies to the criterion set
@@ -331,8 +345,10 @@ GADI_API gadi_status gadi_sweep(const gadi_sweep_instance *instances, int32_t ni
  *                 exceed GADI_NOALLOC_MAX_N (larger n: GADI_ERR_INVALID_ARG).
  *   alpha, omega, eps_inner, max_inner, max_outer: as in gadi_set_params and
  *                 gadi_set_inner.
- *   b, x:         device (or managed) pointers to n FP64 values, owned by the
- *                 caller; x holds x0 on entry and the result on return.
+ *   b, x:         device pointers of the current device (or managed
+ *                 pointers) to n FP64 values, owned by the caller; x holds
+ *                 x0 on entry and the result on return. Memory of another
+ *                 GPU, or host memory, gives GADI_ERR_INVALID_ARG.
  *   cuda_stream:  stream of the work; the call returns after the result is
  *                 in x (the stream is synchronised).
  * Its scratch is one library-owned device array of fixed size (about 9.5 MB),
@@ -341,14 +357,17 @@ GADI_API gadi_status gadi_sweep(const gadi_sweep_instance *instances, int32_t ni
  * done with the device current) and should come before any stream capture.
  * Every call uses the same array and leaves its contents behind: calls that
  * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller. Returns as gadi_solve. */
+ * serialised by the caller. Returns as gadi_solve; info->t_solve_s is the
+ * host wall time of the launch and the synchronisation. */
 #define GADI_NOALLOC_MAX_N 262144
 GADI_API gadi_status gadi_solve_stencil_noalloc(int32_t dim, int32_t N, double beta, double alpha,
                                                 double omega, double eps_inner, int32_t max_inner,
                                                 int32_t max_outer, const double *b, double *x,
                                                 double tol, void *cuda_stream, gadi_info *info);
 
-/* Release all device memory of h. NULL is accepted. */
+/* Release all device memory of h (the copies of A and its splitting that
+ * gadi_create made for Algorithm 1, and the solve's work vectors). NULL is
+ * accepted. */
 GADI_API void gadi_destroy(gadi_solver *h);
 
 GADI_API const char *gadi_status_str(gadi_status s);

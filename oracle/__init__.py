@@ -246,26 +246,6 @@ def gadi_ir(A, b, alpha, omega, tol=1e-13, eps_inner=1e-2, max_inner=200, max_ou
                 prec)
 
 
-def sylvester_matrices(n, r):
-    """The tridiagonal test matrix of §4.3, A = B = M + 2 r N + 100/(n+1)^2 I
-    with M = tridiag(-1, 2, -1) and N = tridiag(0.5, 0, -0.5), as
-    (lo, dg, up) with lo[i] = T[i][i-1], up[i] = T[i][i+1]."""
-    lo = np.full(n, -1.0 + 2.0 * r * 0.5)
-    up = np.full(n, -1.0 + 2.0 * r * (-0.5))
-    dg = np.full(n, 2.0 + 100.0 / (n + 1) ** 2)
-    lo[0] = 0.0
-    up[-1] = 0.0
-    return lo, dg, up
-
-
-def tri_dense(lo, dg, up):
-    n = len(dg)
-    T = np.diag(dg).astype(np.float64)
-    T[np.arange(1, n), np.arange(n - 1)] = lo[1:]
-    T[np.arange(n - 1), np.arange(1, n)] = up[:-1]
-    return T
-
-
 def sylv_norm_inf(a, b):
     m, n = len(a[1]), len(b[1])
     arrs = [_f64(v) for v in (*a, *b)]

@@ -71,6 +71,15 @@ __global__ void k_noalloc_check(int64_t n, const double *b, const double *x, dou
     }
 }
 
+// a failed CUDA call: clear the runtime's last-error state (a non-sticky
+// error such as a rejected launch would otherwise surface in the caller's
+// next CUDA or torch check) and report GADI_ERR_CUDA
+gadi_status cuda_failure()
+{
+    cudaGetLastError();
+    return GADI_ERR_CUDA;
+}
+
 // the address of g_noalloc_scratch on the current device (looked up once)
 cudaError_t scratch_address(int dev, unsigned char **out)
 {
@@ -167,7 +176,7 @@ gadi_status launch(int dev, int num_sms, cudaStream_t stream, unsigned char *bas
     }
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
-    if (e != cudaSuccess || per_sm < 1) return GADI_ERR_CUDA;
+    if (e != cudaSuccess || per_sm < 1) return cuda_failure();
     int64_t need = (nitems + threads - 1) / threads;
     if (nitems <= 16384) need = 1;
     const int blocks = (int)std::min<int64_t>(std::min<int64_t>(need, (int64_t)per_sm * num_sms), kNoallocMaxBlocks);
@@ -205,18 +214,18 @@ gadi_status launch(int dev, int num_sms, cudaStream_t stream, unsigned char *bas
 
     // the control block must start at zero; everything else is written
     // before it is read by the kernel itself
-    if ((e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), stream)) != cudaSuccess) return GADI_ERR_CUDA;
-    const auto t0 = std::chrono::steady_clock::now();
+    if ((e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), stream)) != cudaSuccess) return cuda_failure();
+    const auto t0 = std::chrono::steady_clock::now();   // host wall time (no CUDA events here)
     void *args[] = {(void *)&a};
     if (blocks > 1)
         e = cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(threads), args, 0, stream);
     else
         e = cudaLaunchKernel((const void *)kern, dim3(1), dim3(threads), args, 0, stream);
-    if (e != cudaSuccess) return GADI_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_failure();
     Ctl hc;
     if ((e = cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(stream)) != cudaSuccess)
-        return GADI_ERR_CUDA;
+        return cuda_failure();
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     const gadi_status st = hc.error ? (gadi_status)hc.error : (gadi_status)hc.status;
     if (info) {
@@ -238,14 +247,18 @@ gadi_status launch(int dev, int num_sms, cudaStream_t stream, unsigned char *bas
     return st;
 }
 
-bool device_pointer(const void *p)
+// p is managed memory, or device memory of device dev (the kernels read and
+// write b and x in place on the current device; memory of another GPU is
+// refused rather than dereferenced across devices)
+bool device_pointer(const void *p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -264,13 +277,13 @@ extern "C" gadi_status gadi_solve_stencil_noalloc(int32_t dim, int32_t N, double
     if (!(eps_inner > 0.0 && eps_inner < 1.0) || max_inner < 1 || max_outer < 0)
         return GADI_ERR_INVALID_ARG;
     if (!(tol > 0.0) || !std::isfinite(tol) || !b || !x) return GADI_ERR_INVALID_ARG;
-    if (!device_pointer(b) || !device_pointer(x)) return GADI_ERR_INVALID_ARG;
     int dev = 0, num_sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices ||
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return GADI_ERR_CUDA;
     }
+    if (!device_pointer(b, dev) || !device_pointer(x, dev)) return GADI_ERR_INVALID_ARG;
     unsigned char *base = nullptr;
     if (scratch_address(dev, &base) != cudaSuccess) {
         cudaGetLastError();
@@ -281,13 +294,13 @@ extern "C" gadi_status gadi_solve_stencil_noalloc(int32_t dim, int32_t N, double
     double *chk = (double *)(base + kCtlBytes + kPartBytes);
     int *bad = (int *)(chk + 2);
     double hk[3];
-    if (cudaMemsetAsync(chk, 0, 3 * sizeof(double), stream) != cudaSuccess) return GADI_ERR_CUDA;
+    if (cudaMemsetAsync(chk, 0, 3 * sizeof(double), stream) != cudaSuccess) return cuda_failure();
     const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
     k_noalloc_check<<<g, 256, 0, stream>>>(n, b, x, chk, bad);
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(hk, chk, sizeof hk, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess)
-        return GADI_ERR_CUDA;
+        return cuda_failure();
     int nonfinite;
     std::memcpy(&nonfinite, &hk[2], sizeof(int));
     if (nonfinite) return GADI_ERR_INVALID_ARG;

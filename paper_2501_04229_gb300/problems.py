@@ -232,6 +232,38 @@ def make_problem(dim: int, N: int, beta: float, rhs: str = "manufactured",
 
 # The workloads: sizes, coefficients and right-hand sides of the paper's
 # convection-diffusion experiment, at the grid sizes this library is measured on.
+def sylvester_matrices(n, r):
+    """The tridiagonal test matrix of §4.3's Sylvester experiment, A = B =
+    M + 2 r N + 100/(n+1)^2 I with M = tridiag(-1, 2, -1) and N =
+    tridiag(0.5, 0, -0.5), as (lo, dg, up) with lo[i] = T[i][i-1], up[i] =
+    T[i][i+1] (lo[0] and up[-1] are 0)."""
+    lo = np.full(n, -1.0 + 2.0 * r * 0.5)
+    up = np.full(n, -1.0 + 2.0 * r * (-0.5))
+    dg = np.full(n, 2.0 + 100.0 / (n + 1) ** 2)
+    lo[0] = 0.0
+    up[-1] = 0.0
+    return lo, dg, up
+
+
+def tri_dense(lo, dg, up):
+    """The dense n x n matrix of a (lo, dg, up) tridiagonal triple."""
+    n = len(dg)
+    T = np.diag(dg).astype(np.float64)
+    T[np.arange(1, n), np.arange(n - 1)] = lo[1:]
+    T[np.arange(n - 1), np.arange(1, n)] = up[:-1]
+    return T
+
+
+def sylvester_problem(m, n, r, seed=0):
+    """(a, b, X*, C) for A X + X B = C with the §4.3 matrices of sides m and
+    n, X* standard normal (seeded), C = A X* + X* B in FP64."""
+    a = sylvester_matrices(m, r)
+    b = sylvester_matrices(n, r)
+    Xs = np.random.default_rng(seed).standard_normal((m, n))
+    A, B = tri_dense(*a), tri_dense(*b)
+    return a, b, Xs, A @ Xs + Xs @ B
+
+
 WORKLOADS = {
     # 2D 32x32, beta = 10, b = A*1; plain FP64 GADI anchor
     "convdiff2d_32_b10": dict(dim=2, N=32, beta=10.0, rhs="ones"),

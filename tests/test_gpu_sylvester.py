@@ -8,6 +8,7 @@ import pytest
 import scipy.linalg as sl
 
 import oracle
+from paper_2501_04229_gb300 import problems as P
 from paper_2501_04229_gb300 import gadi as G
 
 pytestmark = pytest.mark.gpu
@@ -30,9 +31,9 @@ PRECS = [(G.GADI_F64, oracle.PREC_DOUBLE), (G.GADI_F32, oracle.PREC_SINGLE), (G.
 
 
 def _case(m, n, r, seed=0):
-    a = oracle.sylvester_matrices(m, r)
-    b = oracle.sylvester_matrices(n, r)
-    A, B = oracle.tri_dense(*a), oracle.tri_dense(*b)
+    a = P.sylvester_matrices(m, r)
+    b = P.sylvester_matrices(n, r)
+    A, B = P.tri_dense(*a), P.tri_dense(*b)
     Xs = np.random.default_rng(seed).standard_normal((m, n))
     return a, b, A, B, A @ Xs + Xs @ B
 

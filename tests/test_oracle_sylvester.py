@@ -8,19 +8,20 @@ import pytest
 import scipy.linalg as sl
 
 import oracle
+from paper_2501_04229_gb300 import problems as P
 
 
 def _case(m, n, r, seed=0):
-    a = oracle.sylvester_matrices(m, r)
-    b = oracle.sylvester_matrices(n, r)
-    A, B = oracle.tri_dense(*a), oracle.tri_dense(*b)
+    a = P.sylvester_matrices(m, r)
+    b = P.sylvester_matrices(n, r)
+    A, B = P.tri_dense(*a), P.tri_dense(*b)
     Xs = np.random.default_rng(seed).standard_normal((m, n))
     return a, b, A, B, A @ Xs + Xs @ B
 
 
 def test_matrices_follow_section_4_3():
-    lo, dg, up = oracle.sylvester_matrices(5, 0.1)
-    T = oracle.tri_dense(lo, dg, up)
+    lo, dg, up = P.sylvester_matrices(5, 0.1)
+    T = P.tri_dense(lo, dg, up)
     M = 2 * np.eye(5) - np.eye(5, k=1) - np.eye(5, k=-1)
     N = 0.5 * np.eye(5, k=-1) - 0.5 * np.eye(5, k=1)
     assert np.array_equal(T, M + 2 * 0.1 * N + 100.0 / 36 * np.eye(5))

@@ -73,3 +73,17 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st, _ = G.gadi_solve_stencil_noalloc(3, 8, 10.0, 1.0, 1.0, np.ascontiguousarray(p.b), np.zeros(p.n),
                                          1e-10)
     assert st == G.GADI_ERR_INVALID_ARG
+
+
+def test_noalloc_refuses_memory_of_another_gpu():
+    # b and x are read and written in place on the current device, so memory
+    # of another GPU must be refused before anything is launched
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs a second visible GPU")
+    torch.cuda.set_device(0)
+    p = P.make_problem(3, 8, 10.0)
+    b = torch.as_tensor(p.b).to(device="cuda:1")
+    x = torch.full((p.n,), 3.0, dtype=torch.float64, device="cuda:1")
+    st, _ = G.gadi_solve_stencil_noalloc(3, 8, 10.0, 1.0, 1.0, b, x, 1e-10)
+    assert st == G.GADI_ERR_INVALID_ARG
+    assert bool((x == 3.0).all())
