@@ -290,22 +290,28 @@ GADI_API void gadi_model_destroy(gadi_model *model);
 GADI_API gadi_status gadi_set_model(gadi_solver *h, int32_t kind, const gadi_model *model);
 
 /* ---- Batched parameter sweep --------------------------------------------
- * Many FP16-inner GADI-IR solves in one persistent launch (captured in a
- * CUDA graph), for building training sets of optimal (alpha, omega) the way
- * §3.3 builds them: from small systems of the same structure.
+ * Many FP16-inner GADI-IR solves in one persistent launch per size bin
+ * (captured in a CUDA graph), for building training sets of optimal (alpha,
+ * omega) the way §3.3 builds them: from small systems of the same structure.
  * Each instance is the constant-coefficient convection-diffusion system of
  * gadi_stencil (variable_k = 0) with b = A 1 and x0 = 0 (as in §4.1); each
  * candidate is an (alpha, omega) pair; every instance is solved with every
  * candidate to eta_inf <= tol (inner eps_inner, max_inner, max_outer as in
- * gadi_set_inner). One block solves one (instance, candidate) item; items
- * of uneven size share the launch, largest first. race != 0 stops a solve
- * once it has used more operator applications than a finished candidate of
- * the same instance (raced_out = 1, status NOT_CONVERGED): it cannot be the
- * cheapest. block_threads: 128, 256 or 512, or 0 for the built-in autotuner
- * (short timed probes, cached per problem class).
+ * gadi_set_inner). A team of blocks solves one (instance, candidate) item;
+ * items of uneven size share the launch of their size bin, largest first.
+ * Schedule: instances are binned by rows (n < 2^15, < 2^18, < 2^20, larger);
+ * each bin has one team size (blocks per item; tried: 1 / 1, 2, 4 / 2, 4, 8
+ * / 4, 8, 16) and one block size (128, 256, 512), chosen by the built-in
+ * autotuner from short timed probes (cached per problem class) unless fixed
+ * by block_threads (128, 256 or 512; 0 = tuned) and team_blocks (1 .. 64;
+ * 0 = tuned). race != 0 stops a solve once it has used more operator
+ * applications than a finished candidate of the same instance (raced_out =
+ * 1, status NOT_CONVERGED): it cannot be the cheapest.
  * records: host array of ninst * ncand entries, written at
  * [instance * ncand + candidate]. Returns OK when every item ran (items
- * carry their own status), INVALID_ARG, OUT_OF_MEMORY or CUDA. */
+ * carry their own status), INVALID_ARG (also: a team larger than the blocks
+ * that fit the GPU at once), OUT_OF_MEMORY, TIMEOUT (a bounded wait of a
+ * team expired) or CUDA. */
 typedef struct {
     int32_t dim, N;
     double beta;
@@ -320,7 +326,7 @@ typedef struct {
     int32_t status;             /* gadi_status of this solve */
     int32_t raced_out;          /* 1 when stopped by the race */
     int32_t outer_iters;
-    int32_t reserved;
+    int32_t team_blocks;        /* blocks of the team that solved this item */
     int64_t inner_iters_H, inner_iters_S, spmv_count;
     double eta_inf;
     double time_ms;             /* device time of this item */
@@ -329,7 +335,8 @@ typedef struct {
 GADI_API gadi_status gadi_sweep(const gadi_sweep_instance *instances, int32_t ninst,
                                 const gadi_sweep_candidate *candidates, int32_t ncand, double tol,
                                 double eps_inner, int32_t max_inner, int32_t max_outer, int32_t race,
-                                int32_t block_threads, void *cuda_stream, gadi_sweep_record *records);
+                                int32_t block_threads, int32_t team_blocks, void *cuda_stream,
+                                gadi_sweep_record *records);
 
 /* Allocation-free solve (the paper has no counterpart: this is a library
  * convenience). Some callers cannot allocate device memory: code that runs

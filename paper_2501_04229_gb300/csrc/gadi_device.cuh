@@ -476,11 +476,14 @@ __device__ __forceinline__ void block_reduce_w0(double (&v)[NS], const int (&ops
 template <int CH>
 struct GridExchangeT {
     Ctl *ctl;
-    double *part;                  // [2][kMaxSlots][gridDim]
+    double *part;                  // [2][kMaxSlots][blocks of the team]
     unsigned epoch;
     unsigned long long wait_ns;
     unsigned extra;                // added to the arrival target (never reached: timeout test)
     bool block_only;               // the team is this block alone (no global memory used)
+    // team of `team` blocks (0: the whole grid) in which this block is
+    // number `rank`: the partials have one slot per team member
+    unsigned team = 0, rank = 0;
 
     template <class V, int NS>
     __device__ __forceinline__ bool allreduce(V (&v)[NS], const int (&ops)[NS])
@@ -489,7 +492,9 @@ struct GridExchangeT {
         V *res = reinterpret_cast<V *>(shd);
         int *s_ok = reinterpret_cast<int *>(shd + 2 * kMaxSlots);
         block_reduce_w0(v, ops);
-        if (block_only || gridDim.x == 1) {
+        const unsigned G = team ? team : gridDim.x;
+        const unsigned me = team ? rank : blockIdx.x;
+        if (block_only || G == 1) {
             if (threadIdx.x == 0)
 #pragma unroll
                 for (int s = 0; s < NS; ++s) res[s] = v[s];
@@ -500,14 +505,13 @@ struct GridExchangeT {
             return true;
         }
         ++epoch;
-        const unsigned G = gridDim.x;
         double *buf = part + (size_t)(epoch & 1u) * kMaxSlots * G;
         if (threadIdx.x < 32) {
             const int lane = threadIdx.x;
             int ok = 1;
             if (lane == 0) {
 #pragma unroll
-                for (int s = 0; s < NS; ++s) buf[(size_t)s * G + blockIdx.x] = (double)v[s];
+                for (int s = 0; s < NS; ++s) buf[(size_t)s * G + me] = (double)v[s];
                 red_release_add_u64(&ctl->arrive, 1ULL);
                 const unsigned long long target = (unsigned long long)epoch * G + extra;
                 const unsigned long long t0 = global_ns();

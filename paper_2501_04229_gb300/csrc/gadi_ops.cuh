@@ -386,12 +386,15 @@ struct EllOp {
     // Rows of width 8 read their columns and values with vector loads and
     // issue all eight gathers before the first product; the products are
     // summed in the same (ascending column) order as for any other width.
-    template <class F>
-    __device__ __forceinline__ void rowsA(int64_t i, const F &f, double (&out)[1]) const
+    // kRes: start from init and subtract every product (init - A x, one
+    // fused multiply-add per term); else A x from zero.
+    template <bool kRes, class F>
+    __device__ __forceinline__ void rowsA_t(int64_t i, const F &f, const double (&init)[1], double (&out)[1]) const
     {
         const int *c = col + i * W;
         const double *v = a64 + i * W;
-        double acc = 0.0;
+        const double sg = kRes ? -1.0 : 1.0;
+        double acc = kRes ? init[0] : 0.0;
         if (W == 8) {
             int cc[8];
             double vv[8], xv[8];
@@ -400,11 +403,23 @@ struct EllOp {
 #pragma unroll
             for (int k = 0; k < 8; ++k) xv[k] = f.one(cc[k]);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc = __fma_rn(vv[k], xv[k], acc);
+            for (int k = 0; k < 8; ++k) acc = __fma_rn(sg * vv[k], xv[k], acc);
         } else {
-            for (int k = 0; k < W; ++k) acc = __fma_rn(__ldg(v + k), f.one(__ldg(c + k)), acc);
+            for (int k = 0; k < W; ++k) acc = __fma_rn(sg * __ldg(v + k), f.one(__ldg(c + k)), acc);
         }
         out[0] = acc;
+    }
+    template <class F>
+    __device__ __forceinline__ void rowsA(int64_t i, const F &f, double (&out)[1]) const
+    {
+        const double z[1] = {0.0};
+        rowsA_t<false>(i, f, z, out);
+    }
+    // r = b - A x for the outer residual (Algorithm 1 step 1)
+    template <class F>
+    __device__ __forceinline__ void resid(int64_t i, const F &f, const double (&b)[1], double (&out)[1]) const
+    {
+        rowsA_t<true>(i, f, b, out);
     }
 
     template <class F>
@@ -504,21 +519,24 @@ struct StencilOp {
     }
 
     // ---- scalar rows (R == 1) ------------------------------------------------
-    template <class F>
-    __device__ __forceinline__ double rowA1(int64_t i, const F &f) const
+    // (A x)_i from zero, or (kRes) init - (A x)_i with every product
+    // subtracted by one fused multiply-add, in the same term order
+    template <bool kRes, class F>
+    __device__ __forceinline__ double rowA1(int64_t i, const F &f, double init = 0.0) const
     {
         unsigned cd[3];
         coords(i, cd);
         const unsigned last = (unsigned)N - 1;
-        double acc = 0.0;
+        const double sg = kRes ? -1.0 : 1.0;
+        double acc = kRes ? init : 0.0;
         const bool face = AD != nullptr;
 #pragma unroll
         for (int d = DIM - 1; d >= 0; --d)
-            if (cd[d] > 0) acc = __fma_rn(face ? __ldg(AL[d] + i) : a_lo, f.one(i - stride(d)), acc);
-        acc = __fma_rn(face ? __ldg(AD + i) : a_diag, f.one(i), acc);
+            if (cd[d] > 0) acc = __fma_rn(sg * (face ? __ldg(AL[d] + i) : a_lo), f.one(i - stride(d)), acc);
+        acc = __fma_rn(sg * (face ? __ldg(AD + i) : a_diag), f.one(i), acc);
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
-            if (cd[d] < last) acc = __fma_rn(face ? __ldg(AU[d] + i) : a_hi, f.one(i + stride(d)), acc);
+            if (cd[d] < last) acc = __fma_rn(sg * (face ? __ldg(AU[d] + i) : a_hi), f.one(i + stride(d)), acc);
         return acc;
     }
 
@@ -566,11 +584,13 @@ struct StencilOp {
     // The FP64 inner path (bound by the FP64 rate, and short of registers
     // for eight FP64 chunks) loads each neighbour where its term is formed.
     static constexpr bool kHoist = !std::is_same<T, double>::value;
-    template <class F>
-    __device__ __forceinline__ void rowsA(int64_t item, const F &f, double (&out)[R]) const
+    // kRes: init - A x (every coefficient negated, which is exact, so each
+    // term is one fused multiply-add subtracting the product); else A x
+    template <bool kRes, class F>
+    __device__ __forceinline__ void rowsA_t(int64_t item, const F &f, const double (&init)[R], double (&out)[R]) const
     {
         if constexpr (R == 1) {
-            out[0] = rowA1(item, f);
+            out[0] = rowA1<kRes>(item, f, init[0]);
         } else {
             constexpr int NB = DIM - 1;
             const int64_t i0 = item * R;
@@ -599,30 +619,32 @@ struct StencilOp {
                 if (hxm) xm = f.one(i0 - 1);
                 if (hxp) xp = f.one(i0 + R);
             }
+            const double sg = kRes ? -1.0 : 1.0;
+            const double clo = sg * a_lo, cdg = sg * a_diag, chi = sg * a_hi;
 #pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] = 0.0;
+            for (int k = 0; k < R; ++k) acc[k] = kRes ? init[k] : 0.0;
 #pragma unroll
             for (int d = DIM - 1; d >= 1; --d)
                 if (hl[d - 1]) {
                     if constexpr (!kHoist) f.template many<R>(i0 - stride(d), tl[d - 1]);
                     if (face) ldv<R>(AL[d], i0, cf);
 #pragma unroll
-                    for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_lo, tl[d - 1][k], acc[k]);
+                    for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? sg * cf[k] : clo, tl[d - 1][k], acc[k]);
                 }
             {   // x lower
                 if (face) ldv<R>(AL[0], i0, cf);
 #pragma unroll
                 for (int k = 0; k < R; ++k)
-                    if (k > 0 || hxm) acc[k] = __fma_rn(face ? cf[k] : a_lo, k ? c[k - 1] : xm, acc[k]);
+                    if (k > 0 || hxm) acc[k] = __fma_rn(face ? sg * cf[k] : clo, k ? c[k - 1] : xm, acc[k]);
             }
             if (face) ldv<R>(AD, i0, cf);
 #pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_diag, c[k], acc[k]);
+            for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? sg * cf[k] : cdg, c[k], acc[k]);
             {   // x upper
                 if (face) ldv<R>(AU[0], i0, cf);
 #pragma unroll
                 for (int k = 0; k < R; ++k)
-                    if (k < R - 1 || hxp) acc[k] = __fma_rn(face ? cf[k] : a_hi, k < R - 1 ? c[k + 1] : xp, acc[k]);
+                    if (k < R - 1 || hxp) acc[k] = __fma_rn(face ? sg * cf[k] : chi, k < R - 1 ? c[k + 1] : xp, acc[k]);
             }
 #pragma unroll
             for (int d = 1; d < DIM; ++d)
@@ -630,11 +652,27 @@ struct StencilOp {
                     if constexpr (!kHoist) f.template many<R>(i0 + stride(d), tu[d - 1]);
                     if (face) ldv<R>(AU[d], i0, cf);
 #pragma unroll
-                    for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? cf[k] : a_hi, tu[d - 1][k], acc[k]);
+                    for (int k = 0; k < R; ++k) acc[k] = __fma_rn(face ? sg * cf[k] : chi, tu[d - 1][k], acc[k]);
                 }
 #pragma unroll
             for (int k = 0; k < R; ++k) out[k] = acc[k];
         }
+    }
+
+    template <class F>
+    __device__ __forceinline__ void rowsA(int64_t item, const F &f, double (&out)[R]) const
+    {
+        double z[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) z[k] = 0.0;
+        rowsA_t<false>(item, f, z, out);
+    }
+    // r = b - A x for the outer residual (Algorithm 1 step 1): b[k] is row
+    // item * R + k of the right-hand side
+    template <class F>
+    __device__ __forceinline__ void resid(int64_t item, const F &f, const double (&b)[R], double (&out)[R]) const
+    {
+        rowsA_t<true>(item, f, b, out);
     }
 
     template <class F>

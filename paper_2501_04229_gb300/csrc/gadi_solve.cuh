@@ -51,7 +51,7 @@ struct SolveArgs {
     Ctl *ctl;
     double *part;                // [2][kMaxSlots][gridDim] partial sums
     double *eta_hist;            // optional, max_outer + 1 entries
-    const long long *race_bound; // optional (one-block teams): stop once spmv exceeds it
+    const long long *race_bound; // optional (batched sweeps): stop once spmv exceeds it
     unsigned long long wait_ns;
     unsigned extra;
 };
@@ -59,11 +59,14 @@ struct SolveArgs {
 // status of a solve stopped by race_bound (reported as not converged)
 constexpr int kRacedOut = 100;
 
-// launch bound: 1024 threads for one-row items, 512 for 4-row and 384 for
-// 8-row items (whose per-thread state is larger: an item holds all its
-// neighbour chunks at once)
+// launch bound: 1024 threads for one-row items, 512 for 4- and 8-row items
+// (whose per-thread state is larger: an item holds all its neighbour chunks
+// at once). For 8-row items 512 threads cap the registers at 128 and the
+// compiler keeps some values in local memory, yet the extra warps hide more
+// memory latency: measured at 192^3, 0.178 s with 384 threads (168
+// registers) against 0.167 s with 512.
 template <class Op>
-__host__ __device__ constexpr int max_threads() { return Op::R > 4 ? 384 : (Op::R > 1 ? 512 : 1024); }
+__host__ __device__ constexpr int max_threads() { return Op::R > 1 ? 512 : 1024; }
 
 // The solve, run by a team of threads: the whole grid (ex.block_only false,
 // t0/nt the global thread index and count) or one block (ex.block_only true,
@@ -87,7 +90,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
     // work vectors: CG uses r (2), u (2), s (2), p, z; CGNR reuses them
     T *const z = a.v[8];
 
-    double r0 = 0.0, best = INFINITY, eta = 0.0, res = 0.0;
+    double r0 = 0.0, best = INFINITY, eta = 0.0, res = 0.0, rinf_prev = 0.0;
     long long itH = 0, itS = 0, spmv = 0;
     int k = 0, status = kErrNotConverged;
     double *xcur = a.x;              // the buffer holding the current iterate
@@ -95,24 +98,35 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
     for (;;) {
         // ---- R: outer residual in FP64 -----------------------------------------
         double vR[3] = {0.0, 0.0, 0.0};
+        // ||r||_2^2 in FP64, or (FP16 / FP8 inner paths stopping on eta_inf,
+        // where ||r||_2 only watches for growth and gives RES for the
+        // record; from the second step on) in FP32 from the round-to-odd
+        // copy scaled by 2^-esq, esq the exponent of the previous ||r||_inf,
+        // so that the squares stay far inside FP32's range
+        const bool sq32 = kDemoteFromOdd<T> && a.stop_kind != 1 && k > 0;
+        const int esq = rinf_prev > 0.0 ? ilogb(rinf_prev) : 0;
         {
-            // the maxima of |r| and |x| as integer maxima of the magnitudes' bit
-            // patterns (same value for finite inputs; FP64 compares issue at
-            // the FP64 rate on this GPU, integer ones at the integer rate)
+            // r = b - A x with each product subtracted by a fused
+            // multiply-add (7 FP64 operations per 7-point row: GB300 issues
+            // FP64 at 2 lanes per clock per SM, so this pass is bound by the
+            // FP64 rate); the maxima of |r| and |x| as integer maxima of the
+            // magnitudes' bit patterns (same value for finite inputs; FP64
+            // compares issue at the FP64 rate, integer ones at the integer
+            // rate)
             double lsum = 0.0;
+            float lsum32 = 0.0f;
+            const float sc32 = ldexpf(1.0f, -max(-126, min(126, esq)));
             uint64_t lmax = 0, xmax = 0;
             constexpr uint64_t kMag = 0x7FFFFFFFFFFFFFFFull;
             const XLoad64 fx{xcur};
             for (int64_t it = t0; it < items; it += nt) {
-                double ax[R], bb[R], xx[R], rr[R];
-                op.rowsA(it, fx, ax);
+                double bb[R], xx[R], rr[R];
                 IO64::ld(a.b, it, bb);
                 IO64::ld(xcur, it, xx);
+                op.resid(it, fx, bb, rr);
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
-                    rr[q] = __dsub_rn(bb[q], ax[q]);
                     lmax = umax64(lmax, bits_of(rr[q]) & kMag);
-                    lsum = __fma_rn(rr[q], rr[q], lsum);
                     xmax = umax64(xmax, bits_of(xx[q]) & kMag);
                 }
                 IO64::st(a.r64, it, rr);
@@ -122,9 +136,20 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
                     for (int q = 0; q < R; ++q) ro[q] = __uint_as_float(float_bits_round_odd(rr[q]));
                     if constexpr (R > 1) stv<R>(a.r32, it * R, ro);
                     else a.r32[it] = ro[0];
+                    if (sq32) {
+#pragma unroll
+                        for (int q = 0; q < R; ++q) {
+                            const float t = __fmul_rn(ro[q], sc32);
+                            lsum32 = __fmaf_rn(t, t, lsum32);
+                        }
+                    }
+                }
+                if (!sq32) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) lsum = __fma_rn(rr[q], rr[q], lsum);
                 }
             }
-            vR[0] = lsum;
+            vR[0] = sq32 ? (double)lsum32 : lsum;
             vR[1] = double_of(lmax);
             vR[2] = double_of(xmax);
         }
@@ -133,24 +158,17 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
             if (!ex.allreduce(vR, opsR)) return;
         }
         ++spmv;
-        const double rinf = vR[1], rn2 = sqrt(vR[0]), xinf = vR[2];
+        const double rinf = vR[1], xinf = vR[2];
+        const double rn2 = sq32 ? ldexp(sqrt(vR[0]), max(-126, min(126, esq))) : sqrt(vR[0]);
+        rinf_prev = rinf;
         const double den = __dadd_rn(__dmul_rn(a.anorm, xinf), a.bnorm);   // as written, not fused
         eta = den > 0.0 ? rinf / den : (rinf == 0.0 ? 0.0 : INFINITY);
         if (k == 0) r0 = rn2;
         res = r0 > 0.0 ? rn2 / r0 : 0.0;
         if (lead && a.eta_hist) a.eta_hist[k] = eta;
-        if (a.race_bound) {
-            // one-block teams only: thread 0 reads the bound, the block agrees
-            __shared__ int s_race;
-            if (threadIdx.x == 0) s_race = spmv > *(const volatile long long *)a.race_bound;
-            __syncthreads();
-            const bool raced = s_race != 0;
-            __syncthreads();
-            if (raced) { status = kRacedOut; break; }
-        }
         {
             bool done = true;
-            if (!isfinite(rn2) || !isfinite(eta)) status = kErrDiverged;
+            if (!isfinite(rn2) || !isfinite(eta) || !isfinite(xinf)) status = kErrDiverged;
             else {
                 if (rn2 < best) best = rn2;
                 const double crit = a.stop_kind == 1 ? res : eta;
@@ -166,7 +184,11 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
         const int e = (a.half && !a.naive && rinf > 0.0) ? ilogb(rinf) : 0;
         T *rc = a.v[0], *rn = a.v[1], *uc = a.v[2], *un = a.v[3];
         T *sc = a.v[4], *sn = a.v[5], *p = a.v[6];
-        Acc g[2] = {0, 0};
+        // g[2]: a raced-out flag (batched sweeps): thread 0 of every block
+        // reads the bound, and the maximum over the team makes the decision
+        // the same in every block
+        Acc g[3] = {0, 0, 0};
+        if (a.race_bound && threadIdx.x == 0 && spmv > *(const volatile long long *)a.race_bound) g[2] = Acc(1);
         auto d_pass = [&](const auto &fr) {
             Acc l0 = 0, l1 = 0;
             for (int64_t it = t0; it < items; it += nt) {
@@ -195,7 +217,11 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
         } else {
             d_pass(XDemote<T>{a.r64, ldexp(1.0, -e)});
         }
-        if (!ex.allreduce(g, ops2)) return;
+        {
+            const int opsD[3] = {kSum, kSum, kMax};
+            if (!ex.allreduce(g, opsD)) return;
+        }
+        if (g[2] > Acc(0)) { status = kRacedOut; break; }
         ++spmv;
         const Acc gam0 = g[0];
 

@@ -1,20 +1,20 @@
 """Evaluation of the parameter predictors on large 3D systems (§3.3).
 
-    python -m paper_2501_04229_gb300.evaluate [--cases 8] [--N 192] [--out results.json]
+    python -m paper_2501_04229_gb300.evaluate [--cases 32] [--N 192] [--out results.json]
 
-Training records come from batched sweeps of small systems of the same
-structure (§3.3 trains on small systems): a 2D set (sides 16..128, beta
-log-uniform in [0.1, 1000]) and a 3D set (sides 8..48, beta log-uniform in
-[1, 500]), each swept over 24 alpha in [0.01, 31.6] x 3 omega to eta_inf <=
-1e-13. From each
-set an MLP (trained on the GPU by the library's kernels) and a GPR are
-fitted. The test systems are the 3D convection-diffusion operator on an
-N^3 grid with beta log-uniform in [1, 500] (seeded, seeds 5000, 5001, ...)
-and the manufactured right-hand side. For every case and predictor: the
-predicted (alpha, omega), the outer and inner iteration counts, operator
-applications and the time to eta_inf <= 1e-13 of FP16-inner GADI-IR, next to
-the best candidate of a grid search on the case itself (the reference for the
-predictors' error).
+Training records come from batched sweeps of smaller systems of the same
+structure (§3.3 trains on small systems): a 3D set (sides 8..160, five
+convection strengths from 2 to 300) -- the set the bench trains on -- and a
+2D set (sides 16..128, beta log-uniform in [0.1, 1000]), each swept over 24
+alpha in [0.1, 31.6] x 3 omega to eta_inf <= 1e-13. From each set an MLP
+(trained on the GPU by the library's kernels) and a GPR are fitted. The test
+systems are the 3D convection-diffusion operator on an N^3 grid with beta
+log-uniform in [1, 500] (case c uses seed 5000 + c) and the manufactured
+right-hand side. For every case and predictor: the predicted (alpha, omega),
+the outer and inner iteration counts, operator applications and the time to
+eta_inf <= 1e-13 of FP16-inner GADI-IR, next to the best candidate of a
+raced grid search on the case itself, 16 alpha = 10^(-3 + 5 j / 15) x 4
+omega in {0, 0.5, 1, 1.5} (the reference for the predictors' error).
 
 Prints a JSON summary and writes all records to --out.
 """
@@ -35,21 +35,23 @@ TOL = 1e-13
 EPS = 0.1
 
 
+THREE_D_TRAIN = [(3, N, b) for N in (8, 16, 24, 32, 48, 64, 96, 128, 160) for b in (2.0, 10.0, 40.0, 100.0, 300.0)]
+
+
 def train_sets(seed=11, records=None):
-    """The 2D training set: swept here (sides 16..128), or read from a record
-    file written by `python -m paper_2501_04229_gb300.sweep` (e.g. 256
-    instances with sides 64..1024); the 3D set is always swept here."""
-    cands = SW.candidates(n_alpha=24, omegas=(0.0, 0.5, 1.0), lo=-2.0, hi=1.5)
+    """The 3D training set (the bench's), and the 2D set: swept here (sides
+    16..128), or read from a record file written by `python -m
+    paper_2501_04229_gb300.sweep` (e.g. 256 instances with sides 64..1024)."""
+    cands = SW.candidates(n_alpha=24, omegas=(0.0, 0.25, 0.5), lo=-1.0, hi=1.5)
     sets = {}
     t0 = time.perf_counter()
+    sets["3d"] = SW.run(THREE_D_TRAIN, cands=cands, eps_inner=EPS, max_outer=4000)
     if records:
         with open(records) as f:
             sets["2d"] = [json.loads(line) for line in f]
     else:
         two = SW.random_instances(48, seed=seed, dim=2, side=(16, 128), beta=(0.1, 1000.0))
         sets["2d"] = SW.run(two, cands=cands, eps_inner=EPS, max_outer=4000)
-    three = SW.random_instances(40, seed=seed + 1, dim=3, side=(8, 48), beta=(1.0, 500.0))
-    sets["3d"] = SW.run(three, cands=cands, eps_inner=EPS, max_outer=4000)
     return sets, time.perf_counter() - t0
 
 
@@ -73,13 +75,14 @@ def solve(h, b, x, alpha, omega, max_outer=100000):
             "spmv_count": info["spmv_count"], "eta_inf": info["eta_inf"], "time_s": info["t_solve_s"]}
 
 
-def grid_optimum(h, b, x, n_alpha=15, omegas=(0.0, 0.5, 1.0)):
-    """Best (fewest operator applications) of an alpha x omega grid on the
-    case itself (alpha in [0.01, 31.6]); each candidate is capped at 1.5x the
-    outer steps of the best one so far, and the grid is walked from alpha =
-    0.3 outwards so that a cap exists early."""
+def grid_optimum(h, b, x, n_alpha=16, omegas=SW.OMEGAS, start=0.3):
+    """Best (fewest operator applications) of the 16 alpha (10^-3 .. 10^2) x
+    4 omega grid on the case itself; each candidate is capped at 1.5x the
+    outer steps of the best one so far (a candidate that needs more cannot
+    be the cheapest unless its inner solves are much cheaper), and the grid
+    is walked from alpha = start outwards so that a cap exists early."""
     best, cap, tried = None, 100000, []
-    for a in sorted(SW.alpha_grid(n_alpha, -2.0, 1.5), key=lambda v: abs(math.log(v / 0.3))):
+    for a in sorted(SW.alpha_grid(n_alpha, -3.0, 2.0), key=lambda v: abs(math.log(v / start))):
         for w in omegas:
             r = solve(h, b, x, a, w, max_outer=cap)
             tried.append(r)
@@ -92,7 +95,7 @@ def grid_optimum(h, b, x, n_alpha=15, omegas=(0.0, 0.5, 1.0)):
 def main(argv=None):
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("--cases", type=int, default=8)
+    ap.add_argument("--cases", type=int, default=32)
     ap.add_argument("--N", type=int, default=192)
     ap.add_argument("--out", default=None)
     ap.add_argument("--records", default=None, help="2D training records (JSONL) instead of a small sweep")
@@ -127,7 +130,7 @@ def main(argv=None):
                     y = G.gadi_model_predict(m, q)[0]
                     a, w = float(math.exp(y[0])), float(min(1.999, max(0.0, y[1])))
                     row[name] = solve(h, b, x, a, w)
-                row["grid"], _ = grid_optimum(h, b, x)
+                row["grid"], _ = grid_optimum(h, b, x, start=row["mlp_3d"]["alpha"] if "mlp_3d" in row else 0.3)
                 results.append(row)
                 print(json.dumps({k: (v if not isinstance(v, dict) else
                                       {kk: v[kk] for kk in ("alpha", "omega", "spmv_count", "time_s", "status")})

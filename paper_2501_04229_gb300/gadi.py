@@ -69,7 +69,7 @@ class gadi_sweep_candidate(C.Structure):
 
 class gadi_sweep_record(C.Structure):
     _fields_ = [("instance", C.c_int32), ("candidate", C.c_int32), ("status", C.c_int32),
-                ("raced_out", C.c_int32), ("outer_iters", C.c_int32), ("reserved", C.c_int32),
+                ("raced_out", C.c_int32), ("outer_iters", C.c_int32), ("team_blocks", C.c_int32),
                 ("inner_iters_H", C.c_int64), ("inner_iters_S", C.c_int64),
                 ("spmv_count", C.c_int64), ("eta_inf", C.c_double), ("time_ms", C.c_double)]
 
@@ -118,7 +118,7 @@ def load(path: str = LIB_PATH):
                                              C.POINTER(gadi_info)]),
         "gadi_last_error": (C.c_char_p, [vp]),
         "gadi_sweep": (i32, [C.POINTER(gadi_sweep_instance), i32, C.POINTER(gadi_sweep_candidate), i32,
-                             f64, f64, i32, i32, i32, i32, vp, C.POINTER(gadi_sweep_record)]),
+                             f64, f64, i32, i32, i32, i32, i32, vp, C.POINTER(gadi_sweep_record)]),
         "gadi_model_fit": (i32, [i32, vp, vp, i32, vp, i32, vp, C.POINTER(vp)]),
         "gadi_model_predict": (i32, [vp, vp, i32, vp]),
         "gadi_model_loss": (i32, [vp, vp, i32, C.POINTER(i32)]),
@@ -278,15 +278,17 @@ def gadi_solve_stencil_noalloc(dim, N, beta, alpha, omega, b, x, tol, eps_inner=
 
 
 def gadi_sweep(instances, candidates, tol=1e-13, eps_inner=0.1, max_inner=200, max_outer=5000,
-               race=True, block_threads=0, stream=None):
+               race=True, block_threads=0, team_blocks=0, stream=None):
     """instances: [(dim, N, beta)], candidates: [(alpha, omega)]. Returns a
-    list of record dicts, one per (instance, candidate), instance-major."""
+    list of record dicts, one per (instance, candidate), instance-major.
+    block_threads / team_blocks: 0 = the autotuned schedule."""
     ni, nc = len(instances), len(candidates)
     I = (gadi_sweep_instance * ni)(*[gadi_sweep_instance(int(d), int(N), float(b)) for d, N, b in instances])
     Cd = (gadi_sweep_candidate * nc)(*[gadi_sweep_candidate(float(a), float(w)) for a, w in candidates])
     R = (gadi_sweep_record * (ni * nc))()
     st = load().gadi_sweep(I, ni, Cd, nc, float(tol), float(eps_inner), int(max_inner), int(max_outer),
-                           int(bool(race)), int(block_threads), C.c_void_p(stream) if stream else None, R)
+                           int(bool(race)), int(block_threads), int(team_blocks),
+                           C.c_void_p(stream) if stream else None, R)
     if st != GADI_OK:
         raise GadiError(st, "gadi_sweep failed")
     return [r.as_dict() for r in R]

@@ -230,8 +230,6 @@ def make_problem(dim: int, N: int, beta: float, rhs: str = "manufactured",
                    A=A, b=b, x_exact=xe, faces=faces)
 
 
-# The workloads: sizes, coefficients and right-hand sides of the paper's
-# convection-diffusion experiment, at the grid sizes this library is measured on.
 def sylvester_matrices(n, r):
     """The tridiagonal test matrix of §4.3's Sylvester experiment, A = B =
     M + 2 r N + 100/(n+1)^2 I with M = tridiag(-1, 2, -1) and N =
@@ -264,6 +262,8 @@ def sylvester_problem(m, n, r, seed=0):
     return a, b, Xs, A @ Xs + Xs @ B
 
 
+# The workloads: sizes, coefficients and right-hand sides of the paper's
+# convection-diffusion experiment, at the grid sizes this library is measured on.
 WORKLOADS = {
     # 2D 32x32, beta = 10, b = A*1; plain FP64 GADI anchor
     "convdiff2d_32_b10": dict(dim=2, N=32, beta=10.0, rhs="ones"),
@@ -271,8 +271,12 @@ WORKLOADS = {
     "convdiff3d_64_b100": dict(dim=3, N=64, beta=100.0, rhs="manufactured"),
     # 3D 128^3, beta = 50, GRF face coefficients (seed 3), manufactured solution
     "convdiff3d_128_b50_grf": dict(dim=3, N=128, beta=50.0, rhs="manufactured", grf_seed=3),
-    # 3D 192^3, beta = 100, manufactured solution: the working set (about 0.5 GB)
-    # is several times the 129 MB L2, so the inner sweeps stream from HBM
+    # 3D 160^3, beta = 100: a smaller system whose working set (about 0.3 GB)
+    # still exceeds the 129 MB L2 (counter captures of the solve kernel)
+    "convdiff3d_160_b100": dict(dim=3, N=160, beta=100.0, rhs="manufactured"),
+    # 3D 192^3, beta = 100, manufactured solution: the working set (about 3 GB
+    # with the solver's vectors) is many times the 129 MB L2, so the inner
+    # sweeps stream from HBM
     "convdiff3d_192_b100": dict(dim=3, N=192, beta=100.0, rhs="manufactured"),
 }
 

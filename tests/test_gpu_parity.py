@@ -506,7 +506,7 @@ def test_e4m3_inner_64cubed_reaches_fp64_floor():
 
 def test_hbm_workload_192cubed_properties():
     """The bench's HBM-bound system (192^3, n = 7.1e6) at full size, in the
-    launch configuration the bench times (automatic: 152 x 384): eta
+    launch configuration the bench times (automatic: 152 x 512): eta
     recomputed by the oracle, and the forward error against the manufactured
     solution within ||r||_2 / lambda_min(M) (A positive real)."""
     p = P.workload("convdiff3d_192_b100")

@@ -1,6 +1,6 @@
-"""Batched GADI-IR sweep (one block per (instance, alpha, omega) item, one
-persistent launch) against single solves through gadi_solve and against the
-oracle."""
+"""Batched GADI-IR sweep (teams of one or more blocks per (instance, alpha,
+omega) item, one persistent launch per size bin) against single solves
+through gadi_solve and against the oracle."""
 import numpy as np
 import pytest
 
@@ -105,3 +105,43 @@ def test_sweep_jsonl_resume(tmp_path):
     assert len(lines) == 2
     assert both[0] == first[0]
     assert both[1]["best"] is not None
+
+
+@pytest.mark.parametrize("team", [2, 4])
+def test_multi_block_teams_match_single_solves(team):
+    """Items solved by teams of several blocks (rows shared over the team's
+    blocks, team-scoped exchanges) agree with gadi_solve like one-block
+    teams do, and with the one-block sweep."""
+    inst = [(2, 64, 30.0), (3, 16, 10.0), (2, 40, 3.0)]
+    cands = [(1.0, 0.0), (3.0, 0.5)]
+    one = G.gadi_sweep(inst, cands, race=False, max_outer=5000, team_blocks=1)
+    many = G.gadi_sweep(inst, cands, race=False, max_outer=5000, team_blocks=team)
+    for i, (d, N, b) in enumerate(inst):
+        for j, (a, w) in enumerate(cands):
+            r1, rk = one[i * len(cands) + j], many[i * len(cands) + j]
+            assert rk["team_blocks"] == team and r1["team_blocks"] == 1
+            assert rk["status"] == r1["status"] == G.GADI_OK and rk["eta_inf"] <= 1e-13
+            _, st, info, _ = _single(d, N, b, a, w)
+            assert abs(rk["outer_iters"] - info["outer_iters"]) <= max(2, 0.15 * info["outer_iters"])
+            assert abs(rk["outer_iters"] - r1["outer_iters"]) <= max(2, 0.15 * r1["outer_iters"])
+
+
+def test_autotuned_schedule_gives_large_instances_multi_block_teams():
+    """The row-bin schedule: an instance of 2^18 or more rows runs on a team
+    of 2 or more blocks, a small one on a single block; racing still keeps
+    the cheapest candidate."""
+    inst = [(3, 64, 100.0), (2, 24, 10.0)]
+    cands = [(0.8, 0.2), (2.0, 0.0), (6.0, 0.0)]
+    recs = G.gadi_sweep(inst, cands, race=True, max_outer=5000)
+    big = recs[:3]
+    small = recs[3:]
+    assert all(r["team_blocks"] >= 2 for r in big)
+    assert all(r["team_blocks"] == 1 for r in small)
+    best = SW.best_candidate(big, cands)
+    full = G.gadi_sweep(inst[:1], cands, race=False, max_outer=5000)
+    assert best["spmv_count"] == SW.best_candidate(full, cands)["spmv_count"]
+
+
+def test_team_larger_than_the_gpu_is_rejected():
+    with pytest.raises(G.GadiError):
+        G.gadi_sweep([(2, 8, 1.0)], [(1.0, 1.0)], team_blocks=65)
