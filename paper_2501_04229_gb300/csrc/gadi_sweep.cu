@@ -3,8 +3,9 @@
 // launch per size bin, captured in a CUDA graph.
 //
 // Teams of k blocks take work items from a global queue (largest systems
-// first) and run one complete FP16-inner GADI-IR solve per item: a team of
-// one block uses block-level reductions only; a team of k > 1 blocks shares
+// first, each instance's candidates from the middle of its list outwards)
+// and run one complete FP16-inner GADI-IR solve per item: a team of one
+// block uses block-level reductions only; a team of k > 1 blocks shares
 // its rows over its blocks and synchronises through a team-scoped exchange
 // (the grid exchange of the solve kernel, on the team's own counter and
 // partials). The system of an item is built on the device from (dim, N,
@@ -25,6 +26,7 @@
 #include <chrono>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -429,8 +431,15 @@ extern "C" gadi_status gadi_sweep(const gadi_sweep_instance *inst, int32_t ninst
         it->maxn = std::max(it->maxn, nrows(i));
     }
     for (auto &g : groups)
-        std::stable_sort(g.items.begin(), g.items.end(),
-                         [&](const SweepItem &a, const SweepItem &b) { return nrows(a.inst) > nrows(b.inst); });
+        // largest systems first; within an instance the candidates from the
+        // middle of the list outwards (the list is ordered by alpha, and the
+        // middle is where optima usually lie), so that a cheap finished
+        // candidate sets the race bound early
+        std::stable_sort(g.items.begin(), g.items.end(), [&](const SweepItem &a, const SweepItem &b) {
+            if (nrows(a.inst) != nrows(b.inst)) return nrows(a.inst) > nrows(b.inst);
+            if (a.inst != b.inst) return a.inst < b.inst;
+            return std::abs(2 * a.cand - (ncand - 1)) < std::abs(2 * b.cand - (ncand - 1));
+        });
 
     DevBuf dinst, dcand, dbest;
     SW_CK(cudaMalloc(&dinst.p, ninst * sizeof(gadi_sweep_instance)));
