@@ -242,6 +242,16 @@ def profiled_traffic(name, algorithmic):
     return round(float(fields["dram-bytes-per-launch"]) * algorithmic / float(fields["algorithmic-bytes-per-launch"]))
 
 
+def solve_kernel_name(kind, info):
+    """The solve kernel a solve ran, from its info (stencil item rows are 8
+    for every bench workload)."""
+    if kind != "stencil":
+        return "gadi_solve_kernel<EllOp<half>>"
+    if info.get("zmarch_planes", 0) > 0:
+        return "gadi_solve_kernel<ZMarchOp<StencilOp<half,3,8>>>"
+    return "gadi_solve_kernel<StencilOp<half,3,8>>"
+
+
 def peaks():
     try:
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -589,7 +599,7 @@ def run_gpu(args, rank, world):
                                   "constant-coefficient stencil application 4 B (FP16 x, y)",
         "traffic_note": "ncu dram bytes of the profiled launch, scaled to this launch by algorithmic bytes; "
                         "null when the kernel changed since the capture",
-        "kernel": ("gadi_solve_kernel<StencilOp<half,3,8>>" if kind == "stencil" else "gadi_solve_kernel<EllOp<half>>"),
+        "kernel": solve_kernel_name(kind, info),
         "kernel_time_s_mean": statistics.mean(kern_t),
         "peak_source": peak_src}
 

@@ -295,6 +295,7 @@ struct gadi_solver {
     int stop = GADI_STOP_ETA;
     int kernel = GADI_KERNEL_AUTO;
     int item_rows = 0;        // stencil rows per item: 0 = automatic, 1, 4 or 8
+    int traversal = 0;        // 0: z-marching solves where available, 1: grid-stride items
     int blocks = 0, threads = 0;
     double wait_ms = 2000.0;
     int force_timeout = 0;
@@ -636,13 +637,37 @@ StencilOp<T, DIM, R> make_stencil(const gadi_solver *h)
     return op;
 }
 
+// the operator object of family Op for the handle's current parameters
+template <class Op, class T>
+Op make_op(gadi_solver *h)
+{
+    if constexpr (std::is_same<Op, EllOp<T>>::value) {
+        return make_ell<T>(h);
+    } else if constexpr (Op::kZMarch) {
+        Op op;
+        static_cast<typename Op::BaseOp &>(op) = make_stencil<T, Op::kDim, Op::R>(h);
+        return op;
+    } else {
+        return make_stencil<T, Op::kDim, Op::R>(h);
+    }
+}
+
+// z-marching segment length for a launch of `lanes` threads on the N^3
+// stencil: about one column segment (N/8 x N columns) per thread, at least
+// 4 planes (0: the march does not pay; use grid-stride items)
+inline int zmarch_len(int N, int64_t lanes)
+{
+    const int64_t cols = (int64_t)(N / 8) * N;
+    const int64_t nseg = std::max<int64_t>(1, lanes / cols);
+    const int zlen = (int)((N + nseg - 1) / nseg);
+    return zlen >= 4 ? zlen : 0;
+}
+
 template <class Op, class T>
 gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, double bnorm,
                       gadi_info *info)
 {
-    Op op;
-    if constexpr (std::is_same<Op, EllOp<T>>::value) op = make_ell<T>(h);
-    else op = make_stencil<T, Op::kDim, Op::R>(h);
+    Op op = make_op<Op, T>(h);
     const int64_t nitems = h->n / Op::R;
 
     auto kern = gadi_solve_kernel<Op, T>;
@@ -671,6 +696,11 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     if (blocks > max_blocks)
         return fail(h, GADI_ERR_INVALID_ARG, "grid_blocks %d exceeds the co-resident maximum %d",
                     blocks, max_blocks);
+    int zlen = 0;
+    if constexpr (Op::kZMarch) {
+        zlen = blocks > 1 ? zmarch_len(op.N, (int64_t)blocks * threads) : 0;
+        if (zlen == 0) return run_solve<typename Op::BaseOp, T>(h, b, x, tol, bnorm, info);
+    }
     if (blocks > h->part_blocks) {
         if (h->part) cudaFree(h->part);
         h->part = nullptr;
@@ -709,6 +739,7 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     a.race_bound = nullptr;
     a.wait_ns = (unsigned long long)(h->wait_ms * 1e6);
     a.extra = h->force_timeout ? 1u : 0u;
+    a.zlen = zlen;
 
     CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
     CK(cudaEventRecord(h->ev0, h->stream));
@@ -739,7 +770,7 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
         info->kernel = std::is_same<Op, EllOp<T>>::value ? GADI_KERNEL_SPARSE : GADI_KERNEL_STENCIL;
         info->grid_blocks = blocks;
         info->block_threads = threads;
-        info->reserved = 0;
+        info->zmarch_planes = zlen;
     }
     if (st == GADI_ERR_TIMEOUT) return fail(h, st, "a device-side grid-barrier wait expired");
     if (st == GADI_ERR_DIVERGED) return fail(h, st, "the iteration diverged (non-finite values, inner breakdown or residual growth)");
@@ -750,9 +781,7 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
 template <class Op, class T>
 gadi_status run_apply(gadi_solver *h, int which, const void *x, void *y)
 {
-    Op op;
-    if constexpr (std::is_same<Op, EllOp<T>>::value) op = make_ell<T>(h);
-    else op = make_stencil<T, Op::kDim, Op::R>(h);
+    Op op = make_op<Op, T>(h);
     const int64_t nitems = h->n / Op::R;
     if constexpr (std::is_same<Op, StencilOp<__half, 3, 8>>::value) {
         // constant-coefficient FP16 stencil without a set launch shape: the
@@ -801,32 +830,39 @@ int item_rows(const gadi_solver *h)
 // the sparse operator, or the stencil for dim 2/3 with items of 1, 4 or 8
 // rows of one grid line
 template <class T, int DIM, class Fn>
-gadi_status dispatch_rows(const gadi_solver *h, Fn &&fn)
+gadi_status dispatch_rows(const gadi_solver *h, Fn &&fn, bool solve)
 {
     switch (item_rows(h)) {
-    case 8: return fn(Tag<StencilOp<T, DIM, 8>>{}, Tag<T>{});
+    case 8:
+        if constexpr (StencilOp<T, DIM, 8>::kZMarchCapable) {
+            // solves of the constant-coefficient operator: the z-marching family
+            if (solve && h->traversal == 0 && !h->variable_k)
+                return fn(Tag<ZMarchOp<StencilOp<T, DIM, 8>>>{}, Tag<T>{});
+        }
+        return fn(Tag<StencilOp<T, DIM, 8>>{}, Tag<T>{});
     case 4: return fn(Tag<StencilOp<T, DIM, 4>>{}, Tag<T>{});
     default: return fn(Tag<StencilOp<T, DIM, 1>>{}, Tag<T>{});
     }
 }
 
 template <class T, class Fn>
-gadi_status dispatch_op(const gadi_solver *h, Fn &&fn)
+gadi_status dispatch_op(const gadi_solver *h, Fn &&fn, bool solve)
 {
     if (!use_stencil(h)) return fn(Tag<EllOp<T>>{}, Tag<T>{});
-    if (h->sdim == 3) return dispatch_rows<T, 3>(h, fn);
-    return dispatch_rows<T, 2>(h, fn);
+    if (h->sdim == 3) return dispatch_rows<T, 3>(h, fn, solve);
+    return dispatch_rows<T, 2>(h, fn, solve);
 }
 
+// solve = true: a solve, which may use the z-marching operator family
 template <class Fn>
-gadi_status dispatch(const gadi_solver *h, Fn &&fn)
+gadi_status dispatch(const gadi_solver *h, Fn &&fn, bool solve = false)
 {
     switch (h->u_r) {
-    case GADI_F16: return dispatch_op<__half>(h, fn);
-    case GADI_BF16: return dispatch_op<__nv_bfloat16>(h, fn);
-    case GADI_E4M3: return dispatch_op<__nv_fp8_e4m3>(h, fn);
-    case GADI_F32: return dispatch_op<float>(h, fn);
-    default: return dispatch_op<double>(h, fn);
+    case GADI_F16: return dispatch_op<__half>(h, fn, solve);
+    case GADI_BF16: return dispatch_op<__nv_bfloat16>(h, fn, solve);
+    case GADI_E4M3: return dispatch_op<__nv_fp8_e4m3>(h, fn, solve);
+    case GADI_F32: return dispatch_op<float>(h, fn, solve);
+    default: return dispatch_op<double>(h, fn, solve);
     }
 }
 
@@ -1085,6 +1121,15 @@ gadi_status gadi_set_scaling(gadi_solver *h, int32_t on)
     return GADI_OK;
 }
 
+gadi_status gadi_set_traversal(gadi_solver *h, int32_t mode)
+{
+    if (!h) return GADI_ERR_INVALID_ARG;
+    if (mode != 0 && mode != 1)
+        return fail(h, GADI_ERR_INVALID_ARG, "traversal must be 0 (automatic) or 1 (grid-stride items)");
+    h->traversal = mode;
+    return GADI_OK;
+}
+
 gadi_status gadi_set_item_rows(gadi_solver *h, int32_t rows)
 {
     if (!h) return GADI_ERR_INVALID_ARG;
@@ -1166,7 +1211,7 @@ gadi_status gadi_solve(gadi_solver *h, const double *b, double *x, double tol, g
         using Op = typename decltype(opk)::type;
         using T = typename decltype(tk)::type;
         return run_solve<Op, T>(h, bb, xx, tol, hb[0], info);
-    });
+    }, true);
     if (st == GADI_ERR_CUDA || st == GADI_ERR_OUT_OF_MEMORY) return st;
     if (!xd) {
         std::string keep = h->err;

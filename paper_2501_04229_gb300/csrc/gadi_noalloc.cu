@@ -211,6 +211,7 @@ gadi_status launch(int dev, int num_sms, cudaStream_t stream, unsigned char *bas
     a.race_bound = nullptr;
     a.wait_ns = 2000000000ULL;
     a.extra = 0;
+    a.zlen = 0;
 
     // the control block must start at zero; everything else is written
     // before it is read by the kernel itself
@@ -242,7 +243,7 @@ gadi_status launch(int dev, int num_sms, cudaStream_t stream, unsigned char *bas
         info->kernel = GADI_KERNEL_STENCIL;
         info->grid_blocks = blocks;
         info->block_threads = threads;
-        info->reserved = 0;
+        info->zmarch_planes = 0;
     }
     return st;
 }

@@ -200,6 +200,52 @@ __device__ __forceinline__ void stv(double *p, int64_t j0, const double (&v)[K])
     for (int k = 0; k < K / 2; ++k) q[k] = make_double2(v[2 * k], v[2 * k + 1]);
 }
 
+// Raw 8-element chunks: the load split from the conversion, so that a
+// chunk can be requested one loop iteration before it is used (z-marching)
+template <class T> struct Raw8;
+template <> struct Raw8<__half> { uint4 u; };
+template <> struct Raw8<float> { float4 a, b; };
+template <> struct Raw8<double> { double2 a, b, c, d; };
+
+__device__ __forceinline__ void ldraw8(const __half *p, int64_t j0, Raw8<__half> &r)
+{
+    r.u = *reinterpret_cast<const uint4 *>(p + j0);
+}
+__device__ __forceinline__ void ldraw8(const float *p, int64_t j0, Raw8<float> &r)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p + j0);
+    r.a = q[0];
+    r.b = q[1];
+}
+__device__ __forceinline__ void ldraw8(const double *p, int64_t j0, Raw8<double> &r)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p + j0);
+    r.a = q[0];
+    r.b = q[1];
+    r.c = q[2];
+    r.d = q[3];
+}
+__device__ __forceinline__ void cvt8(const Raw8<__half> &r, float (&o)[8])
+{
+    const __half2 *h = reinterpret_cast<const __half2 *>(&r.u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 f = __half22float2(h[k]);
+        o[2 * k] = f.x;
+        o[2 * k + 1] = f.y;
+    }
+}
+__device__ __forceinline__ void cvt8(const Raw8<float> &r, float (&o)[8])
+{
+    o[0] = r.a.x; o[1] = r.a.y; o[2] = r.a.z; o[3] = r.a.w;
+    o[4] = r.b.x; o[5] = r.b.y; o[6] = r.b.z; o[7] = r.b.w;
+}
+__device__ __forceinline__ void cvt8(const Raw8<double> &r, double (&o)[8])
+{
+    o[0] = r.a.x; o[1] = r.a.y; o[2] = r.b.x; o[3] = r.b.y;
+    o[4] = r.c.x; o[5] = r.c.y; o[6] = r.d.x; o[7] = r.d.y;
+}
+
 // own-row access of an item of R rows; values rounded to T on store
 template <class T, int R>
 struct ItemIO {
@@ -236,15 +282,20 @@ struct ItemIO64 {
 template <class T>
 struct XLoad {                       // a
     using Acc = typename Prec<T>::Acc;
+    using Val = Acc;
     const T *a;
     __device__ __forceinline__ Acc one(int64_t j) const { return Prec<T>::ld(a[j]); }
     template <int K>
     __device__ __forceinline__ void many(int64_t j0, Acc (&o)[K]) const { ldv<K>(a, j0, o); }
+    struct Raw { Raw8<T> v; };
+    __device__ __forceinline__ void load8(int64_t j0, Raw &w) const { ldraw8(a, j0, w.v); }
+    __device__ __forceinline__ void eval8(const Raw &w, Acc (&o)[8]) const { cvt8(w.v, o); }
 };
 
 template <class T>
 struct XAxpy {                       // fl(a + c b)
     using Acc = typename Prec<T>::Acc;
+    using Val = Acc;
     using P = Prec<T>;
     const T *a, *b;
     Acc c;
@@ -258,11 +309,26 @@ struct XAxpy {                       // fl(a + c b)
         P::madd_s(o, x, c, y);
         P::rndv(o);
     }
+    struct Raw { Raw8<T> v[2]; };
+    __device__ __forceinline__ void load8(int64_t j0, Raw &w) const
+    {
+        ldraw8(a, j0, w.v[0]);
+        ldraw8(b, j0, w.v[1]);
+    }
+    __device__ __forceinline__ void eval8(const Raw &w, Acc (&o)[8]) const
+    {
+        Acc x[8], y[8];
+        cvt8(w.v[0], x);
+        cvt8(w.v[1], y);
+        P::madd_s(o, x, c, y);
+        P::rndv(o);
+    }
 };
 
 template <class T>
 struct XAxpy2 {                      // fl(a - c fl(b + d e))  (C-G residual update, fused)
     using Acc = typename Prec<T>::Acc;
+    using Val = Acc;
     using P = Prec<T>;
     const T *a, *b, *e;
     Acc c, d;
@@ -283,11 +349,30 @@ struct XAxpy2 {                      // fl(a - c fl(b + d e))  (C-G residual upd
         P::madd_s(o, x, -c, w);
         P::rndv(o);
     }
+    struct Raw { Raw8<T> v[3]; };
+    __device__ __forceinline__ void load8(int64_t j0, Raw &r) const
+    {
+        ldraw8(a, j0, r.v[0]);
+        ldraw8(b, j0, r.v[1]);
+        ldraw8(e, j0, r.v[2]);
+    }
+    __device__ __forceinline__ void eval8(const Raw &r, Acc (&o)[8]) const
+    {
+        Acc x[8], y[8], w[8];
+        cvt8(r.v[0], x);
+        cvt8(r.v[1], y);
+        cvt8(r.v[2], w);
+        P::madd_s(w, y, d, w);
+        P::rndv(w);
+        P::madd_s(o, x, -c, w);
+        P::rndv(o);
+    }
 };
 
 template <class T>
 struct XScale {                      // fl(c a): c a power of two, or (2-w) a in the unscaled mode
     using Acc = typename Prec<T>::Acc;
+    using Val = Acc;
     using P = Prec<T>;
     const T *a;
     Acc c;
@@ -300,13 +385,32 @@ struct XScale {                      // fl(c a): c a power of two, or (2-w) a in
         P::mul_s(o, c, x);
         P::rndv(o);
     }
+    struct Raw { Raw8<T> v; };
+    __device__ __forceinline__ void load8(int64_t j0, Raw &w) const { ldraw8(a, j0, w.v); }
+    __device__ __forceinline__ void eval8(const Raw &w, Acc (&o)[8]) const
+    {
+        Acc x[8];
+        cvt8(w.v, x);
+        P::mul_s(o, c, x);
+        P::rndv(o);
+    }
 };
 
 template <class T>
 struct XDemote {                     // fl_T(2^-e r), r in FP64 (Alg. 1: r^ = fl_r(s^))
     using Acc = typename Prec<T>::Acc;
+    using Val = Acc;
     const double *r;
     double sc;                       // 2^-e
+    struct Raw { Raw8<double> v; };
+    __device__ __forceinline__ void load8(int64_t j0, Raw &w) const { ldraw8(r, j0, w.v); }
+    __device__ __forceinline__ void eval8(const Raw &w, Acc (&o)[8]) const
+    {
+        double x[8];
+        cvt8(w.v, x);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = Prec<T>::ld(Prec<T>::from64(sc == 1.0 ? x[k] : x[k] * sc));
+    }
     __device__ __forceinline__ Acc one(int64_t j) const
     {
         return Prec<T>::ld(Prec<T>::from64(sc == 1.0 ? r[j] : r[j] * sc));
@@ -327,6 +431,7 @@ struct XDemote {                     // fl_T(2^-e r), r in FP64 (Alg. 1: r^ = fl
 // where entries below the FP32 normal range round to zero either way)
 template <class T>
 struct XDemoteOdd {
+    using Val = float;
     const float *r32;
     float sc;                        // 2^-e
     __device__ __forceinline__ float one(int64_t j) const
@@ -343,13 +448,28 @@ struct XDemoteOdd {
 #pragma unroll
         for (int k = 0; k < K; ++k) o[k] = x[k];
     }
+    struct Raw { Raw8<float> v; };
+    __device__ __forceinline__ void load8(int64_t j0, Raw &w) const { ldraw8(r32, j0, w.v); }
+    __device__ __forceinline__ void eval8(const Raw &w, float (&o)[8]) const
+    {
+        float x[8];
+        cvt8(w.v, x);
+        Prec<__half>::mul_s(x, sc, x);
+        Prec<T>::rndv(x);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = x[k];
+    }
 };
 
 struct XLoad64 {
+    using Val = double;
     const double *a;
     __device__ __forceinline__ double one(int64_t j) const { return a[j]; }
     template <int K>
     __device__ __forceinline__ void many(int64_t j0, double (&o)[K]) const { ldv<K>(a, j0, o); }
+    struct Raw { Raw8<double> v; };
+    __device__ __forceinline__ void load8(int64_t j0, Raw &w) const { ldraw8(a, j0, w.v); }
+    __device__ __forceinline__ void eval8(const Raw &w, double (&o)[8]) const { cvt8(w.v, o); }
 };
 
 // ---------------------------------------------------------------------------
@@ -364,6 +484,7 @@ template <class T>
 struct EllOp {
     using Acc = typename Prec<T>::Acc;
     static constexpr int R = 1;
+    static constexpr bool kZMarch = false;          // grid-stride rows only
     int64_t n;
     int W;
     const int *__restrict__ col;
@@ -516,6 +637,123 @@ struct StencilOp {
     __device__ __forceinline__ int64_t stride(int d) const
     {
         return d == 0 ? 1 : (d == 1 ? (int64_t)N : (int64_t)N * N);
+    }
+
+    // ---- z-marching rows (3D, constant coefficients, 8-row items) ------------
+    // A thread marches along z through one column of items (the 8-row chunk
+    // of an x-line at fixed y): the values of the planes below and above
+    // (zl, zu) and its own (c) come from the march; only the y neighbours
+    // and the two x ends are loaded. The terms and their order are those of
+    // rows() and resid(), so every row has the same bits.
+    static constexpr bool kZMarchCapable = DIM == 3 && RR == 8 && std::is_same<T, __half>::value;
+    static constexpr bool kZMarch = false;          // grid-stride items (ZMarchOp marches)
+    struct ZCol {                     // the column's boundary flags (fixed along z)
+        bool hly, huy, hxm, hxp;
+    };
+    __device__ __forceinline__ ZCol zcol(int64_t col) const
+    {
+        const unsigned nx8 = (unsigned)N / 8;
+        const unsigned y = (unsigned)col / nx8, xc = (unsigned)col - y * nx8;
+        const unsigned last = (unsigned)N - 1;
+        return ZCol{y > 0, y < last, xc > 0, xc * 8 + 8 <= last};
+    }
+    template <class F, class V>
+    __device__ __forceinline__ void zm_gather(int64_t i0, const ZCol &zc, const F &f, V (&yl)[8], V (&yu)[8],
+                                              V &xm, V &xp) const
+    {
+        if (zc.hly) {
+            f.template many<8>(i0 - N, yl);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) yl[k] = V(0);
+        }
+        if (zc.huy) {
+            f.template many<8>(i0 + N, yu);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) yu[k] = V(0);
+        }
+        xm = zc.hxm ? f.one(i0 - 1) : V(0);
+        xp = zc.hxp ? f.one(i0 + 8) : V(0);
+    }
+    template <class F>
+    __device__ __forceinline__ void rows_zm(int which, int64_t item, const F &f, const ZCol &zc, bool hlz, bool huz,
+                                            const Acc (&c)[8], const Acc (&zl)[8], const Acc (&zu)[8],
+                                            Acc (&out)[8]) const
+    {
+        using P = Prec<T>;
+        const int64_t i0 = item * 8;
+        Acc yl[8], yu[8], xm, xp, acc[8], sh[8];
+        zm_gather(i0, zc, f, yl, yu, xm, xp);
+        if (which == kOpH) {
+            P::mul_s(acc, sigH, c);
+            if (hlz) P::madd_s(acc, acc, h_off, zl);
+            if (zc.hly) P::madd_s(acc, acc, h_off, yl);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sh[k] = k ? c[k - 1] : xm;
+            P::madd_s(acc, acc, h_off, sh);
+            P::madd_s(acc, acc, h_diag, c);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sh[k] = k < 7 ? c[k + 1] : xp;
+            P::madd_s(acc, acc, h_off, sh);
+            if (zc.huy) P::madd_s(acc, acc, h_off, yu);
+            if (huz) P::madd_s(acc, acc, h_off, zu);
+        } else {
+            const Acc lo = which == kOpS ? -s_c : s_c;
+            P::mul_s(acc, sigS, c);
+            if (hlz) P::madd_s(acc, acc, lo, zl);
+            if (zc.hly) P::madd_s(acc, acc, lo, yl);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sh[k] = k ? c[k - 1] : xm;
+            P::madd_s(acc, acc, lo, sh);
+            if (s_diag != Acc(0)) P::madd_s(acc, acc, s_diag, c);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sh[k] = k < 7 ? c[k + 1] : xp;
+            P::madd_s(acc, acc, -lo, sh);
+            if (zc.huy) P::madd_s(acc, acc, -lo, yu);
+            if (huz) P::madd_s(acc, acc, -lo, zu);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out[k] = acc[k];
+    }
+    // r = b - A x along the march (FP64 x values c, zl, zu)
+    template <class F>
+    __device__ __forceinline__ void resid_zm(int64_t item, const F &f, const ZCol &zc, bool hlz, bool huz,
+                                             const double (&c)[8], const double (&zl)[8], const double (&zu)[8],
+                                             const double (&b)[8], double (&out)[8]) const
+    {
+        const int64_t i0 = item * 8;
+        double yl[8], yu[8], xm, xp, acc[8];
+        zm_gather(i0, zc, f, yl, yu, xm, xp);
+        const double clo = -a_lo, cdg = -a_diag, chi = -a_hi;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = b[k];
+        if (hlz) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(clo, zl[k], acc[k]);
+        }
+        if (zc.hly) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(clo, yl[k], acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k > 0 || zc.hxm) acc[k] = __fma_rn(clo, k ? c[k - 1] : xm, acc[k]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(cdg, c[k], acc[k]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < 7 || zc.hxp) acc[k] = __fma_rn(chi, k < 7 ? c[k + 1] : xp, acc[k]);
+        if (zc.huy) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(chi, yu[k], acc[k]);
+        }
+        if (huz) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = __fma_rn(chi, zu[k], acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out[k] = acc[k];
     }
 
     // ---- scalar rows (R == 1) ------------------------------------------------
@@ -796,6 +1034,17 @@ struct StencilOp {
             for (int k = 0; k < R; ++k) out[k] = acc[k];
         }
     }
+};
+
+// The stencil operator with the z-marching traversal compiled in: its own
+// instantiation of the solve kernel (the passes march along z and nothing
+// else), so that the grid-stride instantiation keeps its own register
+// allocation.
+template <class Base>
+struct ZMarchOp : Base {
+    using BaseOp = Base;
+    static_assert(Base::kZMarchCapable, "z-marching needs the 3D FP16 stencil with 8-row items");
+    static constexpr bool kZMarch = true;
 };
 
 }  // namespace gadi

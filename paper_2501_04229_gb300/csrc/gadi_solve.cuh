@@ -54,6 +54,311 @@ struct SolveArgs {
     const long long *race_bound; // optional (batched sweeps): stop once spmv exceeds it
     unsigned long long wait_ns;
     unsigned extra;
+    int zlen;                    // z-marching operator family: planes per column segment
+};
+
+// ---------------------------------------------------------------------------
+// z-marching traversal of the 8-row items (3D constant-coefficient FP16
+// stencil, operator family ZMarchOp). A unit of work is one column of items
+// (the 8-row chunk of an x-line at fixed y) over zlen consecutive planes;
+// thread t takes units t, t + nt, ... The values of the expression f at
+// planes z-1, z, z+1 come from the march (the raw chunk of plane z+2 is
+// requested while plane z is worked on), so only the y neighbours and the x
+// ends are loaded per plane; the pass's own vectors (loader O) are requested
+// one plane ahead. work(it, zc, z, c, zl, zu, own) forms the rows of item
+// it; the passes' work objects below keep their partial sums as members.
+// ---------------------------------------------------------------------------
+struct OwnNone {
+    struct Raw {};
+    __device__ __forceinline__ void load8(int64_t, Raw &) const {}
+};
+
+template <class T, int NV>
+struct OwnVec {                      // the first nload of NV inner-precision vectors
+    const T *v[NV];
+    int nload;
+    struct Raw { Raw8<T> r[NV]; };
+    __device__ __forceinline__ void load8(int64_t j0, Raw &w) const
+    {
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nload) ldraw8(v[k], j0, w.r[k]);
+    }
+};
+
+template <class T, int NV>
+struct OwnVecX {                     // NV inner-precision vectors and one FP64 vector
+    const T *v[NV];
+    const double *x;
+    struct Raw { Raw8<T> r[NV]; Raw8<double> d; };
+    __device__ __forceinline__ void load8(int64_t j0, Raw &w) const
+    {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) ldraw8(v[k], j0, w.r[k]);
+        ldraw8(x, j0, w.d);
+    }
+};
+
+template <class Op, class F, class O, class Work>
+__device__ __forceinline__ void zmarch_items(const Op &op, int zlen, int64_t t0, int64_t nt, const F &f,
+                                             const O &own, Work &work)
+{
+    using V = typename F::Val;
+    const int N = op.N, last = N - 1;
+    const int64_t cols = (int64_t)(N / 8) * N;
+    const int nseg = (N + zlen - 1) / zlen;
+    const int64_t units = cols * nseg;
+    for (int64_t u = t0; u < units; u += nt) {
+        const int64_t col = u % cols;
+        const int z0 = (int)(u / cols) * zlen, z1 = min(N, z0 + zlen);
+        const auto zc = op.zcol(col);
+        typename F::Raw fr{};
+        typename O::Raw ocur{}, onext{};
+        V zl[8], c[8], zu[8];
+        if (z0 > 0) {
+            f.load8((col + (int64_t)(z0 - 1) * cols) * 8, fr);
+            f.eval8(fr, zl);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) zl[k] = V(0);
+        }
+        f.load8((col + (int64_t)z0 * cols) * 8, fr);
+        f.eval8(fr, c);
+        if (z0 < last) f.load8((col + (int64_t)(z0 + 1) * cols) * 8, fr);
+        own.load8((col + (int64_t)z0 * cols) * 8, ocur);
+        for (int z = z0; z < z1; ++z) {
+            if (z < last) {
+                f.eval8(fr, zu);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) zu[k] = V(0);
+            }
+            if (z + 2 <= last && z + 1 < z1) f.load8((col + (int64_t)(z + 2) * cols) * 8, fr);
+            if (z + 1 < z1) own.load8((col + (int64_t)(z + 1) * cols) * 8, onext);
+            work(col + (int64_t)z * cols, zc, z, c, zl, zu, ocur);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                zl[k] = c[k];
+                c[k] = zu[k];
+            }
+            ocur = onext;
+        }
+    }
+}
+
+// The passes of one outer step along the march (same arithmetic as the
+// grid-stride passes of solve_body, which describes them).
+template <class Op, class T>
+struct ZmResid {                     // R: r = b - A x, maxima, round-to-odd copy, ||r||_2^2
+    const Op *op;
+    const XLoad64 *f;
+    double *r64;
+    float *r32;
+    int last;
+    bool sq32;
+    float sc32;
+    double lsum = 0.0;
+    float lsum32 = 0.0f;
+    uint64_t lmax = 0, xmax = 0;
+    __device__ __forceinline__ void operator()(int64_t it, const typename Op::ZCol &zc, int zi, const double (&c)[8],
+                                               const double (&zl)[8], const double (&zu)[8],
+                                               const XLoad64::Raw &ob)
+    {
+        constexpr uint64_t kMag = 0x7FFFFFFFFFFFFFFFull;
+        double bb[8], rr[8];
+        cvt8(ob.v, bb);
+        op->resid_zm(it, *f, zc, zi > 0, zi < last, c, zl, zu, bb, rr);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            lmax = umax64(lmax, bits_of(rr[q]) & kMag);
+            xmax = umax64(xmax, bits_of(c[q]) & kMag);
+        }
+        ItemIO64<8>::st(r64, it, rr);
+        if constexpr (kDemoteFromOdd<T>) {
+            float ro[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) ro[q] = __uint_as_float(float_bits_round_odd(rr[q]));
+            stv<8>(r32, it * 8, ro);
+            if (sq32) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float t = __fmul_rn(ro[q], sc32);
+                    lsum32 = __fmaf_rn(t, t, lsum32);
+                }
+            }
+        }
+        if (!sq32) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) lsum = __fma_rn(rr[q], rr[q], lsum);
+        }
+    }
+};
+
+template <class Op, class T, class F>
+struct ZmDemote {                    // D: r^ = fl(2^-e r), u = H' r^, z = 0
+    using Acc = typename Prec<T>::Acc;
+    using P = Prec<T>;
+    const Op *op;
+    const F *f;
+    T *rc, *uc, *z;
+    int last;
+    Acc l0 = 0, l1 = 0;
+    __device__ __forceinline__ void operator()(int64_t it, const typename Op::ZCol &zc, int zi, const Acc (&c)[8],
+                                               const Acc (&zl)[8], const Acc (&zu)[8], const OwnNone::Raw &)
+    {
+        Acc uu[8], zz[8];
+        op->rows_zm(kOpH, it, *f, zc, zi > 0, zi < last, c, zl, zu, uu);
+        P::rndv(uu);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            zz[q] = Acc(0);
+            l0 = P::madd(l0, c[q], c[q]);
+            l1 = P::madd(l1, uu[q], c[q]);
+        }
+        ItemIO<T, 8>::st(rc, it, c);
+        ItemIO<T, 8>::st(uc, it, uu);
+        ItemIO<T, 8>::st(z, it, zz);
+    }
+};
+
+template <class Op, class T, class F>
+struct ZmCG {                        // CG pass (single reduction): p, s, z, r', u' = H' r'
+    using Acc = typename Prec<T>::Acc;
+    using P = Prec<T>;
+    const Op *op;
+    const F *f;
+    T *p, *sn, *z, *rn, *un;
+    bool first;
+    Acc al, be;
+    int last;
+    Acc l0 = 0, l1 = 0, zm = 0;
+    __device__ __forceinline__ void operator()(int64_t it, const typename Op::ZCol &zc, int zi, const Acc (&c)[8],
+                                               const Acc (&zl)[8], const Acc (&zu)[8],
+                                               const typename OwnVec<T, 5>::Raw &ow)
+    {
+        Acc r_[8], u_[8], z_[8], p_[8], s_[8], rnew[8], unew[8];
+        cvt8(ow.r[0], r_);
+        cvt8(ow.r[1], u_);
+        cvt8(ow.r[2], z_);
+        if (first) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { p_[q] = r_[q]; s_[q] = u_[q]; }
+        } else {
+            cvt8(ow.r[3], p_);
+            cvt8(ow.r[4], s_);
+            P::madd_s(p_, r_, be, p_);
+            P::madd_s(s_, u_, be, s_);
+            P::rndv(p_);
+            P::rndv(s_);
+        }
+        op->rows_zm(kOpH, it, *f, zc, zi > 0, zi < last, c, zl, zu, unew);
+        P::madd_s(z_, z_, al, p_);
+        P::madd_s(rnew, r_, -al, s_);
+        P::rndv(z_);
+        P::rndv(rnew);
+        P::rndv(unew);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            l0 = P::madd(l0, rnew[q], rnew[q]);
+            l1 = P::madd(l1, unew[q], rnew[q]);
+            zm = fmax(zm, fabs(z_[q]));
+        }
+        ItemIO<T, 8>::st(p, it, p_);
+        ItemIO<T, 8>::st(sn, it, s_);
+        ItemIO<T, 8>::st(z, it, z_);
+        ItemIO<T, 8>::st(rn, it, rnew);
+        ItemIO<T, 8>::st(un, it, unew);
+    }
+};
+
+template <class Op, class T, class F>
+struct ZmC0 {                        // C0: z^ = 2^-ez z, s = S'^T z^, p = s, y = 0
+    using Acc = typename Prec<T>::Acc;
+    using P = Prec<T>;
+    const Op *op;
+    const F *f;
+    T *rsc, *s, *pc, *y;
+    int last;
+    Acc l0 = 0, l1 = 0;
+    __device__ __forceinline__ void operator()(int64_t it, const typename Op::ZCol &zc, int zi, const Acc (&c)[8],
+                                               const Acc (&zl)[8], const Acc (&zu)[8], const OwnNone::Raw &)
+    {
+        Acc ss[8], yy[8];
+        op->rows_zm(kOpST, it, *f, zc, zi > 0, zi < last, c, zl, zu, ss);
+        P::rndv(ss);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            yy[j] = Acc(0);
+            l0 = P::madd(l0, c[j], c[j]);
+            l1 = P::madd(l1, ss[j], ss[j]);
+        }
+        ItemIO<T, 8>::st(rsc, it, c);
+        ItemIO<T, 8>::st(s, it, ss);
+        ItemIO<T, 8>::st(pc, it, ss);
+        ItemIO<T, 8>::st(y, it, yy);
+    }
+};
+
+template <class Op, class T, class F>
+struct ZmCgnrA {                     // CGNR pass A: p = s + be p (stored unless first), q = S' p
+    using Acc = typename Prec<T>::Acc;
+    using P = Prec<T>;
+    const Op *op;
+    const F *f;
+    T *pn, *q;
+    bool store_p;
+    int last;
+    Acc l0 = 0;
+    __device__ __forceinline__ void operator()(int64_t it, const typename Op::ZCol &zc, int zi, const Acc (&c)[8],
+                                               const Acc (&zl)[8], const Acc (&zu)[8], const OwnNone::Raw &)
+    {
+        Acc qq[8];
+        if (store_p) ItemIO<T, 8>::st(pn, it, c);
+        op->rows_zm(kOpS, it, *f, zc, zi > 0, zi < last, c, zl, zu, qq);
+        P::rndv(qq);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) l0 = P::madd(l0, qq[j], qq[j]);
+        ItemIO<T, 8>::st(q, it, qq);
+    }
+};
+
+template <class Op, class T, class F>
+struct ZmCgnrB {                     // CGNR pass B: y += ac p, rs' = rs - ac q, s = S'^T rs', x update
+    using Acc = typename Prec<T>::Acc;
+    using P = Prec<T>;
+    const Op *op;
+    const F *f;
+    T *y, *rsn, *s;
+    double *xnext;
+    Acc ac;
+    double upd;
+    int last;
+    Acc l0 = 0, l1 = 0;
+    __device__ __forceinline__ void operator()(int64_t it, const typename Op::ZCol &zc, int zi, const Acc (&c)[8],
+                                               const Acc (&zl)[8], const Acc (&zu)[8],
+                                               const typename OwnVecX<T, 2>::Raw &ow)
+    {
+        Acc yy[8], pp[8], ss[8];
+        double xx[8];
+        cvt8(ow.r[0], yy);
+        cvt8(ow.r[1], pp);
+        cvt8(ow.d, xx);
+        op->rows_zm(kOpST, it, *f, zc, zi > 0, zi < last, c, zl, zu, ss);
+        P::madd_s(yy, yy, ac, pp);
+        P::rndv(yy);
+        P::rndv(ss);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xx[j] = __fma_rn(upd, P::to64(yy[j]), xx[j]);
+        ItemIO64<8>::st(xnext, it, xx);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            l0 = P::madd(l0, c[j], c[j]);
+            l1 = P::madd(l1, ss[j], ss[j]);
+        }
+        ItemIO<T, 8>::st(y, it, yy);
+        ItemIO<T, 8>::st(rsn, it, c);
+        ItemIO<T, 8>::st(s, it, ss);
+    }
 };
 
 // status of a solve stopped by race_bound (reported as not converged)
@@ -119,6 +424,14 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
             uint64_t lmax = 0, xmax = 0;
             constexpr uint64_t kMag = 0x7FFFFFFFFFFFFFFFull;
             const XLoad64 fx{xcur};
+            if constexpr (Op::kZMarch) {
+                ZmResid<Op, T> w{&op, &fx, a.r64, a.r32, op.N - 1, sq32, sc32};
+                zmarch_items(op, a.zlen, t0, nt, fx, XLoad64{a.b}, w);
+                lsum = w.lsum;
+                lsum32 = w.lsum32;
+                lmax = w.lmax;
+                xmax = w.xmax;
+            } else
             for (int64_t it = t0; it < items; it += nt) {
                 double bb[R], xx[R], rr[R];
                 IO64::ld(a.b, it, bb);
@@ -210,7 +523,21 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
             g[0] = l0;
             g[1] = l1;
         };
-        if constexpr (kDemoteFromOdd<T>) {
+        if constexpr (Op::kZMarch) {
+            if (e >= -100 && e <= 126) {
+                const XDemoteOdd<T> fr{a.r32, ldexpf(1.0f, -e)};
+                ZmDemote<Op, T, XDemoteOdd<T>> w{&op, &fr, rc, uc, z, op.N - 1};
+                zmarch_items(op, a.zlen, t0, nt, fr, OwnNone{}, w);
+                g[0] = w.l0;
+                g[1] = w.l1;
+            } else {
+                const XDemote<T> fr{a.r64, ldexp(1.0, -e)};
+                ZmDemote<Op, T, XDemote<T>> w{&op, &fr, rc, uc, z, op.N - 1};
+                zmarch_items(op, a.zlen, t0, nt, fr, OwnNone{}, w);
+                g[0] = w.l0;
+                g[1] = w.l1;
+            }
+        } else if constexpr (kDemoteFromOdd<T>) {
             // from the round-to-odd FP32 copy where that is exact, else from FP64
             if (e >= -100 && e <= 126) d_pass(XDemoteOdd<T>{a.r32, ldexpf(1.0f, -e)});
             else d_pass(XDemote<T>{a.r64, ldexp(1.0, -e)});
@@ -277,8 +604,28 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
                     w3[1] = l1;
                     w3[2] = zm;
                 };
-                if (first) cg_pass(XAxpy<T>{rc, uc, -al});
-                else cg_pass(XAxpy2<T>{rc, uc, sc, al, be});
+                if constexpr (Op::kZMarch) {
+                    const OwnVec<T, 5> own{{rc, uc, z, p, sc}, first ? 3 : 5};
+                    if (first) {
+                        const XAxpy<T> fx{rc, uc, -al};
+                        ZmCG<Op, T, XAxpy<T>> w{&op, &fx, p, sn, z, rn, un, first, al, be, op.N - 1};
+                        zmarch_items(op, a.zlen, t0, nt, fx, own, w);
+                        w3[0] = w.l0;
+                        w3[1] = w.l1;
+                        w3[2] = w.zm;
+                    } else {
+                        const XAxpy2<T> fx{rc, uc, sc, al, be};
+                        ZmCG<Op, T, XAxpy2<T>> w{&op, &fx, p, sn, z, rn, un, first, al, be, op.N - 1};
+                        zmarch_items(op, a.zlen, t0, nt, fx, own, w);
+                        w3[0] = w.l0;
+                        w3[1] = w.l1;
+                        w3[2] = w.zm;
+                    }
+                } else if (first) {
+                    cg_pass(XAxpy<T>{rc, uc, -al});
+                } else {
+                    cg_pass(XAxpy2<T>{rc, uc, sc, al, be});
+                }
                 if (!ex.allreduce(w3, ops3)) return;
                 ++it_cg;
                 ++spmv;
@@ -309,6 +656,12 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
             // z^ = 2^-ez z; unscaled mode: (2-w) a z formed in the inner precision
             const XScale<T> fz{z, a.naive ? (Acc)a.pfac : (Acc)ldexp(1.0, -ez)};
             Acc l0 = 0, l1 = 0;
+            if constexpr (Op::kZMarch) {
+                ZmC0<Op, T, XScale<T>> w{&op, &fz, rsc, s, pc, y, op.N - 1};
+                zmarch_items(op, a.zlen, t0, nt, fz, OwnNone{}, w);
+                l0 = w.l0;
+                l1 = w.l1;
+            } else
             for (int64_t it = t0; it < items; it += nt) {
                 Acc rs[R], ss[R], yy[R];
                 if constexpr (R > 1) fz.template many<R>(it * R, rs);
@@ -349,7 +702,19 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
                 Acc u1[1] = {0};
                 {
                     Acc l0 = 0;
-                    if (first) {
+                    if constexpr (Op::kZMarch) {
+                        if (first) {
+                            const XLoad<T> fp{pc};
+                            ZmCgnrA<Op, T, XLoad<T>> w{&op, &fp, pn, q, false, op.N - 1};
+                            zmarch_items(op, a.zlen, t0, nt, fp, OwnNone{}, w);
+                            l0 = w.l0;
+                        } else {
+                            const XAxpy<T> fp{s, pc, be};
+                            ZmCgnrA<Op, T, XAxpy<T>> w{&op, &fp, pn, q, true, op.N - 1};
+                            zmarch_items(op, a.zlen, t0, nt, fp, OwnNone{}, w);
+                            l0 = w.l0;
+                        }
+                    } else if (first) {
                         const XLoad<T> fp{pc};
                         for (int64_t it = t0; it < items; it += nt) {
                             Acc qq[R];
@@ -387,6 +752,12 @@ __device__ __forceinline__ void solve_body(const SolveArgs<Op, T> &a, Ex &ex, co
                 {
                     const XAxpy<T> frs{rsc, q, -ac};
                     Acc l0 = 0, l1 = 0;
+                    if constexpr (Op::kZMarch) {
+                        ZmCgnrB<Op, T, XAxpy<T>> w{&op, &frs, y, rsn, s, xnext, ac, upd, op.N - 1};
+                        zmarch_items(op, a.zlen, t0, nt, frs, OwnVecX<T, 2>{{y, pc}, xcur}, w);
+                        l0 = w.l0;
+                        l1 = w.l1;
+                    } else
                     for (int64_t it = t0; it < items; it += nt) {
                         Acc yy[R], pp[R], rn_[R], ss[R];
                         double xx[R];

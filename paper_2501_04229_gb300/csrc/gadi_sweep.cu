@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(512, 1) gadi_sweep_kernel(const SweepArgs s)
         a.race_bound = s.race ? s.best + wi.inst : nullptr;
         a.wait_ns = s.wait_ns;
         a.extra = 0;
+        a.zlen = 0;
         const unsigned long long t_start = global_ns();
         solve_body(a, ex, t0, nt, lead);
         __syncthreads();

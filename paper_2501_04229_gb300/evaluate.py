@@ -16,7 +16,9 @@ eta_inf <= 1e-13 of FP16-inner GADI-IR, next to the best candidate of a
 raced grid search on the case itself, 16 alpha = 10^(-3 + 5 j / 15) x 4
 omega in {0, 0.5, 1, 1.5} (the reference for the predictors' error).
 
-Prints a JSON summary and writes all records to --out.
+Prints one JSON line per case and a summary line. --out receives the same
+as JSON lines (every case's full records as soon as the case ends, the
+summary last), so an interrupted run keeps the cases it finished.
 """
 from __future__ import annotations
 
@@ -111,6 +113,7 @@ def main(argv=None):
         for kind, m in ms.items():
             models[f"{kind}_{name}"] = m
     results = []
+    out = open(args.out, "w") if args.out else None
     try:
         for c in range(args.cases):
             rng = np.random.default_rng(5000 + c)
@@ -132,6 +135,9 @@ def main(argv=None):
                     row[name] = solve(h, b, x, a, w)
                 row["grid"], _ = grid_optimum(h, b, x, start=row["mlp_3d"]["alpha"] if "mlp_3d" in row else 0.3)
                 results.append(row)
+                if out:
+                    out.write(json.dumps(row) + "\n")
+                    out.flush()
                 print(json.dumps({k: (v if not isinstance(v, dict) else
                                       {kk: v[kk] for kk in ("alpha", "omega", "spmv_count", "time_s", "status")})
                                   for k, v in row.items()}), flush=True)
@@ -140,22 +146,30 @@ def main(argv=None):
     finally:
         for m in models.values():
             G.gadi_model_destroy(m)
-    summary = {"cases": len(results), "N": args.N, "train_records": counts, "sweep_s": round(t_sweep, 2)}
-    for name in models:
+    summary = summarize(results, list(models))
+    summary.update({"N": args.N, "train_records": counts, "sweep_s": round(t_sweep, 2)})
+    if out:
+        out.write(json.dumps({"summary": summary}) + "\n")
+        out.close()
+    print(json.dumps(summary))
+
+
+def summarize(results, names):
+    """Per predictor: cases converged, and the means over them of operator
+    applications, outer steps and time relative to the grid's best, and of
+    the time itself."""
+    summary = {"cases": len(results)}
+    for name in names:
         ok = [r for r in results if r[name]["status"] == "GADI_OK" and r["grid"]]
         if ok:
-            summary[name] = {
-                "converged": len(ok),
-                "spmv_vs_grid_mean": float(np.mean([r[name]["spmv_count"] / r["grid"]["spmv_count"] for r in ok])),
-                "time_vs_grid_mean": float(np.mean([r[name]["time_s"] / r["grid"]["time_s"] for r in ok])),
-                "time_s_mean": float(np.mean([r[name]["time_s"] for r in ok]))}
+            rel = lambda key: float(np.mean([r[name][key] / r["grid"][key] for r in ok]))
+            summary[name] = {"converged": len(ok), "spmv_vs_grid_mean": rel("spmv_count"),
+                             "outer_vs_grid_mean": rel("outer_iters"), "time_vs_grid_mean": rel("time_s"),
+                             "time_s_mean": float(np.mean([r[name]["time_s"] for r in ok]))}
         else:
             summary[name] = {"converged": 0}
     summary["grid_time_s_mean"] = float(np.mean([r["grid"]["time_s"] for r in results if r["grid"]]))
-    if args.out:
-        with open(args.out, "w") as f:
-            json.dump({"summary": summary, "cases": results}, f, indent=1)
-    print(json.dumps(summary))
+    return summary
 
 
 if __name__ == "__main__":

@@ -26,7 +26,7 @@ OP_A, OP_H, OP_S, OP_ST = 0, 1, 2, 3
 
 # every entry point declared in include/gadi.h
 EXPORTS = [
-    "gadi_create", "gadi_set_params", "gadi_set_inner", "gadi_set_stop", "gadi_set_kernel", "gadi_set_item_rows", "gadi_set_scaling",
+    "gadi_create", "gadi_set_params", "gadi_set_inner", "gadi_set_stop", "gadi_set_kernel", "gadi_set_item_rows", "gadi_set_traversal", "gadi_set_scaling",
     "gadi_set_launch", "gadi_set_wait_limit", "gadi_debug_force_timeout", "gadi_solve",
     "gadi_apply", "gadi_get_scales", "gadi_predict_params", "gadi_destroy", "gadi_status_str",
     "gadi_last_error", "gadi_solve_stencil_noalloc", "gadi_sweep", "gadi_model_fit",
@@ -53,7 +53,7 @@ class gadi_info(C.Structure):
                 ("spmv_count", C.c_int64), ("eta_inf", C.c_double), ("res_rel", C.c_double),
                 ("t_solve_s", C.c_double), ("scale_exp_M", C.c_int32), ("scale_exp_N", C.c_int32),
                 ("kernel", C.c_int32), ("grid_blocks", C.c_int32), ("block_threads", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("zmarch_planes", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -74,7 +74,7 @@ class gadi_sweep_record(C.Structure):
                 ("spmv_count", C.c_int64), ("eta_inf", C.c_double), ("time_ms", C.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class GadiError(RuntimeError):
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
         "gadi_set_stop": (i32, [vp, i32]),
         "gadi_set_kernel": (i32, [vp, i32]),
         "gadi_set_item_rows": (i32, [vp, i32]),
+        "gadi_set_traversal": (i32, [vp, i32]),
         "gadi_set_scaling": (i32, [vp, i32]),
         "gadi_set_launch": (i32, [vp, i32, i32]),
         "gadi_set_wait_limit": (i32, [vp, f64]),
@@ -217,6 +218,10 @@ def gadi_set_kernel(h, kind):
 
 def gadi_set_item_rows(h, rows):
     _check(h, load().gadi_set_item_rows(h, int(rows)))
+
+
+def gadi_set_traversal(h, mode):
+    _check(h, load().gadi_set_traversal(h, int(mode)))
 
 
 def gadi_set_scaling(h, on):

@@ -1,7 +1,7 @@
 """Repeated solves of one workload, for counter captures of the solve kernel.
 
     python -m paper_2501_04229_gb300.profile_solve --workload convdiff3d_160_b100 \\
-        [--alpha 0.8] [--omega 0.2] [--eps 0.1] [--max-outer M] [--solves 3] [--kernel stencil]
+        [--alpha 0.8] [--omega 0.2] [--eps 0.1] [--max-outer M] [--solves 3] [--kernel stencil] [--traversal 0]
 
 Each solve runs from x0 = 0 with FP16 inner solves (one persistent launch
 of gadi_solve_kernel). --max-outer caps the outer steps (0: the launch does
@@ -30,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--max-outer", type=int, default=100000)
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--kernel", default="stencil", choices=["stencil", "sparse"])
+    ap.add_argument("--traversal", type=int, default=0, choices=[0, 1],
+                    help="0: z-marching where available, 1: grid-stride items")
     args = ap.parse_args(argv)
     from . import build
     build.build()
@@ -42,6 +44,7 @@ def main(argv=None):
         G.gadi_set_kernel(h, G.GADI_KERNEL_STENCIL if args.kernel == "stencil" else G.GADI_KERNEL_SPARSE)
         G.gadi_set_params(h, args.alpha, args.omega, u_r=G.GADI_F16)
         G.gadi_set_inner(h, args.eps, 500, args.max_outer)
+        G.gadi_set_traversal(h, args.traversal)
         b = dev(p.b)
         x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
         for i in range(args.solves):
@@ -52,7 +55,7 @@ def main(argv=None):
             print(json.dumps({"solve": i, "workload": args.workload, "n": p.n, "status": G.status_str(st),
                               **{k: info[k] for k in ("outer_iters", "inner_iters_H", "inner_iters_S",
                                                       "spmv_count", "eta_inf", "t_solve_s", "grid_blocks",
-                                                      "block_threads")}}), flush=True)
+                                                      "block_threads", "zmarch_planes")}}), flush=True)
     finally:
         G.gadi_destroy(h)
 
