@@ -374,7 +374,7 @@ GADI_API gadi_status gadi_sweep(const gadi_sweep_instance *instances, int32_t ni
  * Its scratch is one library-owned device array of fixed size (about 9.5 MB),
  * present on every GPU that loads the library until the process exits; the
  * first call on a device looks up that array's address (a one-time set-up
- * done with the device current) and should come before any stream capture.
+ * done with the device current).
  * Every call uses the same array and leaves its contents behind: calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller. Returns as gadi_solve; info->t_solve_s is the
