@@ -778,6 +778,9 @@ gadi_status run_solve(gadi_solver *h, const double *b, double *x, double tol, do
     return st;
 }
 
+// ring slots (planes) of the staged stencil application
+constexpr int kStagedSlots = 8;
+
 template <class Op, class T>
 gadi_status run_apply(gadi_solver *h, int which, const void *x, void *y)
 {
@@ -785,17 +788,26 @@ gadi_status run_apply(gadi_solver *h, int which, const void *x, void *y)
     const int64_t nitems = h->n / Op::R;
     if constexpr (std::is_same<Op, StencilOp<__half, 3, 8>>::value) {
         // constant-coefficient FP16 stencil without a set launch shape: the
-        // z-marching kernel, with segments of at least 4 planes and about
-        // two 256-thread blocks per SM in all
-        if (!h->threads && !h->blocks && op.HD == nullptr && which != kOpA) {
-            const int64_t lines = (int64_t)(op.N / 8) * op.N;
-            const int64_t want = (int64_t)2 * 256 * h->num_sms;
-            const int64_t nzs = std::max<int64_t>(1, std::min<int64_t>(op.N / 4, want / lines));
-            const int zlen = (int)((op.N + nzs - 1) / nzs);
-            const int64_t segs = (op.N + zlen - 1) / zlen;
-            const unsigned blocks = (unsigned)((lines * segs + 255) / 256);
-            gadi_apply_zmarch_kernel<Op><<<blocks, 256, 0, h->stream>>>(op, which, zlen, (const __half *)x,
-                                                                        (__half *)y);
+        // shared-memory staged kernel when a block can own ty >= 4 whole
+        // y-lines (ty divides N, nx8 ty <= 512 threads), with z segments of
+        // at least 4 planes and about two blocks per SM in all
+        const int nx8 = op.N / 8;
+        int ty = 0;
+        if (nx8 <= 128)
+            for (int t = 512 / nx8; t >= 4; --t)
+                if (op.N % t == 0) { ty = t; break; }
+        if (!h->threads && !h->blocks && op.HD == nullptr && which != kOpA && ty) {
+            constexpr int S = kStagedSlots;
+            const int ytiles = op.N / ty;
+            const int64_t want = (2 * (int64_t)h->num_sms + ytiles - 1) / ytiles;
+            const int nseg = (int)std::max<int64_t>(1, std::min<int64_t>(op.N / 4, want));
+            const int zlen = (op.N + nseg - 1) / nseg;
+            const int segs = (op.N + zlen - 1) / zlen;
+            const size_t smem = (size_t)S * (ty + 2) * nx8 * sizeof(uint4);
+            auto kern = gadi_apply_staged_kernel<Op, S>;
+            CK(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<(unsigned)(ytiles * segs), (unsigned)(nx8 * ty), smem, h->stream>>>(
+                op, which, ty, zlen, (const __half *)x, (__half *)y);
             CK(cudaGetLastError());
             return GADI_OK;
         }

@@ -739,15 +739,6 @@ __global__ void __maxnreg__(128) gadi_apply_kernel_wide(const Op op, int64_t nit
     apply_body<Op, T>(op, nitems, which, xv, yv);
 }
 
-// Operator application for the constant-coefficient 3D stencil with FP16
-// vectors and 8-row items, marching along z: a thread takes the 8-row chunk
-// of one x-line at (x0, y) for a segment of zlen consecutive planes. The
-// chunks of planes z-1, z and z+1 stay in registers from one plane to the
-// next, so a plane costs one new 16-byte read (the chunk three planes
-// ahead, in flight while the thread works on the current plane); the y
-// neighbours and the x ends of the next plane are read one plane ahead.
-// Each row is formed with the terms of StencilOp::rows in the same order,
-// so the result is bit for bit that of gadi_apply_kernel.
 __device__ __forceinline__ void half8_to_float(const uint4 &u, float (&o)[8])
 {
     const __half2 *h = reinterpret_cast<const __half2 *>(&u);
@@ -759,55 +750,82 @@ __device__ __forceinline__ void half8_to_float(const uint4 &u, float (&o)[8])
     }
 }
 
-template <class Op>
-__global__ void __launch_bounds__(256, 2) gadi_apply_zmarch_kernel(const Op op, int which, int zlen,
-                                                                    const __half *x, __half *y)
+// 16-byte asynchronous copy global -> shared (cp.async, bypassing L1) and
+// its group bookkeeping
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
-    static_assert(Op::kDim == 3 && Op::R == 8, "3D stencil with 8-row items");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Operator application for the constant-coefficient 3D stencil with FP16
+// vectors and 8-row items, staged through shared memory. A block owns ty
+// consecutive y-lines (all nx8 = N/8 chunks of each, one thread per chunk)
+// for a segment of zlen planes and streams the planes through a ring of S
+// shared-memory slots: each slot holds the block's ty lines of one plane
+// plus the y-lines just below and above them (halo), copied with 16-byte
+// cp.async by the threads that own them (threads of rows 0 and 1 copy the
+// two halo lines). Planes z-1, z, z+1 are read from the ring while S-4
+// later planes are in flight, so the block keeps (S-3) x (ty+2) x nx8 x 16
+// bytes requested without holding them in registers; a thread's own chunk
+// of planes z-1 and z stays converted in registers from the previous plane,
+// so a plane costs three chunk conversions (z+1 and the two y neighbours). Each row is formed
+// with the terms of StencilOp::rows in the same order, so the result is
+// bit for bit that of gadi_apply_kernel. Shared memory: S (ty+2) nx8 16 B.
+template <class Op, int S>
+__global__ void __launch_bounds__(512, 2) gadi_apply_staged_kernel(const Op op, int which, int ty, int zlen,
+                                                                   const __half *x, __half *y)
+{
+    static_assert(Op::kDim == 3 && Op::R == 8 && S >= 4, "3D stencil with 8-row items");
     using P = Prec<__half>;
     constexpr int R = 8;
-    const int N = op.N;
-    const int nx8 = N / R;
+    extern __shared__ uint4 ring[];
+    const int N = op.N, nx8 = N / R, last = N - 1;
     const int64_t NN = (int64_t)N * N;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int cx = (int)(g % nx8);
-    const int64_t t = g / nx8;
-    const int yy = (int)(t % N);
-    const int64_t seg = t / N;
-    if (seg * zlen >= N) return;
-    const int z0 = (int)(seg * zlen);
+    const int ytiles = N / ty;
+    const int y0 = (int)(blockIdx.x % ytiles) * ty;
+    const int z0 = (int)(blockIdx.x / ytiles) * zlen;
     const int z1 = min(N, z0 + zlen);
-    const int last = N - 1;
-    const int64_t base = (int64_t)cx * R + (int64_t)yy * N;   // row of (x0, y, z = 0)
-    const bool hly = yy > 0, huy = yy < last;
-    const bool hxm = cx > 0, hxp = cx * R + R <= last;
-    // neighbour offsets, clamped to the item itself where the grid ends
-    const int64_t oyl = hly ? -(int64_t)N : 0, oyu = huy ? (int64_t)N : 0;
-    const int64_t oxm = hxm ? -1 : 0, oxp = hxp ? R : 0;
-    auto chunk = [&](int z, int64_t off) { return *reinterpret_cast<const uint4 *>(x + base + off + (int64_t)z * NN); };
-
-    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-    uint4 rm = z0 > 0 ? chunk(z0 - 1, 0) : zero4;              // plane z - 1
-    uint4 r0 = chunk(z0, 0);                                     // plane z
-    uint4 r1 = chunk(min(z0 + 1, last), 0);                      // plane z + 1
-    uint4 r2 = chunk(min(z0 + 2, min(z1, last)), 0);             // plane z + 2
-    uint4 ryl = chunk(z0, oyl), ryu = chunk(z0, oyu);            // y neighbours of plane z
-    __half hxl = x[base + oxm + (int64_t)z0 * NN], hxu = x[base + oxp + (int64_t)z0 * NN];
+    const int cx = (int)threadIdx.x % nx8, r = (int)threadIdx.x / nx8;   // blockDim.x = nx8 * ty
+    const int yy = y0 + r;
+    const int lines = ty + 2;
+    // copies of plane zp (planes z0-1 .. z1 inside the grid are needed)
+    auto load_plane = [&](int zp) {
+        if (zp < 0 || zp > last || zp > z1) return;
+        uint4 *slot = ring + (size_t)((zp + 1 - z0) % S) * lines * nx8;
+        const __half *row = x + (int64_t)zp * NN + (int64_t)yy * N + cx * R;
+        cp_async16(slot + (r + 1) * nx8 + cx, row);
+        if (r == 0 && y0 > 0) cp_async16(slot + cx, row - N);                                    // y0 - 1
+        if (r == 1 && y0 + ty <= last) cp_async16(slot + (ty + 1) * nx8 + cx, row + (int64_t)(ty - 1) * N);  // y0 + ty
+    };
+    for (int k = 0; k < S - 1; ++k) {
+        load_plane(z0 - 1 + k);
+        cp_async_commit();
+    }
+    const bool hly = yy > 0, huy = yy < last, hxm = cx > 0, hxp = cx < nx8 - 1;
+    const int plane = lines * nx8, own_off = (r + 1) * nx8 + cx;
+    float zl[R], c[R];               // this thread's chunk of planes z - 1 and z, carried
     for (int z = z0; z < z1; ++z) {
-        // reads for later planes first: the chunk three planes ahead (never
-        // beyond the plane after the segment), the next plane's y and x reads
-        const uint4 r3 = chunk(min(z + 3, min(z1, last)), 0);
-        const int zq = min(z + 1, z1 - 1);
-        const uint4 nyl = chunk(zq, oyl), nyu = chunk(zq, oyu);
-        const __half nxl = x[base + oxm + (int64_t)zq * NN], nxu = x[base + oxp + (int64_t)zq * NN];
-
-        float c[R], zl[R], zu[R], yl[R], yu[R], acc[R], sh[R];
-        half8_to_float(rm, zl);
-        half8_to_float(r0, c);
-        half8_to_float(r1, zu);
-        half8_to_float(ryl, yl);
-        half8_to_float(ryu, yu);
-        const float xm = hxm ? P::ld(hxl) : 0.0f, xp = hxp ? P::ld(hxu) : 0.0f;
+        // the groups of planes up to z + 1 are complete when at most S - 4
+        // of the (S - 1) + (z - z0) committed ones are pending
+        cp_async_wait<S - 4>();
+        __syncthreads();
+        const unsigned q = (unsigned)(z - z0);
+        const uint4 *pc = ring + (size_t)((q + 1u) % S) * plane;   // plane z
+        const uint4 *pu = ring + (size_t)((q + 2u) % S) * plane;   // plane z + 1
+        if (z == z0) {
+            half8_to_float(ring[(size_t)(q % S) * plane + own_off], zl);   // plane z - 1
+            half8_to_float(pc[own_off], c);
+        }
+        float zu[R], yl[R], yu[R], acc[R], sh[R];
+        half8_to_float(pu[own_off], zu);
+        half8_to_float(pc[r * nx8 + cx], yl);
+        half8_to_float(pc[(r + 2) * nx8 + cx], yu);
+        const __half *own = reinterpret_cast<const __half *>(pc + (own_off - cx));
+        const float xm = hxm ? P::ld(own[cx * R - 1]) : 0.0f, xp = hxp ? P::ld(own[cx * R + R]) : 0.0f;
         const bool hlz = z > 0, huz = z < last;
         if (which == kOpH) {
             P::mul_s(acc, op.sigH, c);
@@ -837,17 +855,17 @@ __global__ void __launch_bounds__(256, 2) gadi_apply_zmarch_kernel(const Op op, 
             if (huy) P::madd_s(acc, acc, -lo, yu);
             if (huz) P::madd_s(acc, acc, -lo, zu);
         }
-        ItemIO<__half, R>::st(y, (base + (int64_t)z * NN) / R, acc);
-
-        rm = r0;
-        r0 = r1;
-        r1 = r2;
-        r2 = r3;
-        ryl = nyl;
-        ryu = nyu;
-        hxl = nxl;
-        hxu = nxu;
+        ItemIO<__half, R>::st(y, ((int64_t)z * NN + (int64_t)yy * N + cx * R) / R, acc);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            zl[k] = c[k];
+            c[k] = zu[k];
+        }
+        __syncthreads();             // every thread is done with plane z - 1's slot
+        load_plane(z + S - 2);       // into that slot
+        cp_async_commit();
     }
+    cp_async_wait<0>();
 }
 
 }  // namespace gadi

@@ -144,13 +144,16 @@ def test_apply_item_rows_bit_exact(name, rows, u_r):
         G.gadi_destroy(h)
 
 
-@pytest.mark.parametrize("N", [24, 48, 96])
-def test_apply_zmarch_bit_exact(N):
-    """The z-marching FP16 stencil application (8-row items, a segment of z
-    planes per thread, chunks carried from plane to plane in registers)
-    gives the oracle's application bit for bit, and the same bits as the
-    one-item-per-thread kernel that a set launch shape selects; N = 24, 48,
-    96 give 6, 12 and 24 segments per z-line and several blocks."""
+@pytest.mark.parametrize("N", [24, 48, 96, 176])
+def test_apply_staged_bit_exact(N):
+    """The shared-memory staged FP16 stencil application (a block owns whole
+    y-lines of a z segment; planes stream through a ring of shared-memory
+    slots filled by cp.async, with halo lines above and below) gives the
+    oracle's application bit for bit, and the same bits as the
+    one-item-per-thread kernel that a set launch shape selects. N = 24, 48:
+    one block of y-lines per segment, 6 and 12 segments; N = 96: 3 blocks
+    of 32 y-lines per plane, 24 segments; N = 176: 8 blocks of 22 y-lines,
+    segments of 5 planes with a last one of 1 plane."""
     p = P.make_problem(3, N, 60.0)
     h = _handle(p)
     try:
@@ -516,8 +519,9 @@ def test_hbm_workload_192cubed_properties():
         G.gadi_set_inner(h, 0.1, 500, 100000)
         st, info, x = _solve(h, p, 1e-13)
         assert st == G.GADI_OK and info["grid_blocks"] * info["block_threads"] >= 152 * 256
-        # the bench's operator application at this size (z-marching kernel,
-        # 12-plane segments) against the one-item-per-thread kernel
+        # the bench's operator application at this size (staged kernel, 12
+        # blocks of 16 y-lines, 8-plane segments) against the
+        # one-item-per-thread kernel
         xh = torch.randn(p.n, device="cuda").half()
         for which in (G.OP_H, G.OP_S, G.OP_ST):
             y1 = torch.empty_like(xh)
