@@ -194,14 +194,16 @@ GADI_API gadi_status gadi_set_item_rows(gadi_solver *h, int32_t rows);
 /* Traversal of the solve kernel's passes (an implementation choice, not
  * part of the paper's method): 0 = automatic (default): solves of the 3D
  * constant-coefficient stencil with FP16 inner vectors and 8-row items use
- * the z-marching kernel, in which every thread marches along z through a
- * column of items (the 8-row chunk of an x-line at fixed y) over a segment
- * of at least 4 planes, keeping the values of planes z-1, z, z+1 in
- * registers and requesting plane z+2 while plane z is formed; other solves,
- * and launches too small for segments of 4 planes, use grid-stride items.
- * 1 = grid-stride items always. Every row is formed with the same terms in
- * the same order either way; the dot products of a solve sum in another
- * order. Other values return INVALID_ARG. */
+ * the z-marching kernel, whose residual, demotion, CGNR-start and CGNR-A
+ * passes march along z: every thread takes a column of items (the 8-row
+ * chunk of an x-line at fixed y) over a segment of at least 4 planes,
+ * keeping the values of planes z-1, z, z+1 in registers and requesting
+ * plane z+2 while plane z is formed (its CG and CGNR-B passes take
+ * grid-stride items); other solves, and launches too small for segments of
+ * 4 planes, use grid-stride items in every pass (gadi_info.zmarch_planes =
+ * 0). 1 = grid-stride items always. Every row is formed with the same
+ * terms in the same order either way; the dot products of a solve sum in
+ * another order. Other values return INVALID_ARG. */
 GADI_API gadi_status gadi_set_traversal(gadi_solver *h, int32_t mode);
 
 /* Launch shape of the persistent solve kernel: grid_blocks (0 = automatic,
