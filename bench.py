@@ -52,7 +52,7 @@ SECONDARY = "convdiff3d_64_b100"
 TOL = 1e-13
 # inner relative tolerance of the timed FP16-inner solves: the best of
 # 0.3, 0.2, 0.1, 0.05, 0.03, 0.01 on the 192^3 system at the predicted
-# (alpha, omega) (0.05: 279 outer steps, 0.151 s; 0.1: 309, 0.158 s)
+# (alpha, omega) (0.05: 279 outer steps, 0.145 s; 0.1: 311, 0.154 s)
 EPS16 = 5e-2
 # inner tolerance of the training sweeps (the records of the evaluation and
 # of the sweep workload use the same) and of FP8 E4M3 inner solves (4
