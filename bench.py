@@ -760,15 +760,24 @@ def oracle_steps(p, alpha, omega, eps, max_outer):
     return time.perf_counter() - t0, info
 
 
+def oracle_setup_s(p, alpha, omega, eps):
+    """Seconds of an oracle call that stops at its first residual (the
+    splitting, the allocations and one residual): the part of a call that
+    does not grow with its outer steps, so that a sample of k steps scales
+    to n steps as setup + (t - setup) n / k. The faster of two calls."""
+    return min(oracle_steps(p, alpha, omega, eps, 0)[0] for _ in range(2))
+
+
 def cpu_baseline(p, alpha, omega, eps, budget_s, gpu_outer=None):
     """The oracle (FP64-inner GADI-IR, all host cores) on the same system and
     parameters: a full solve when it fits the budget (estimated from two outer
-    steps), else as many outer steps as fit, scaled per outer step to the
-    outer-step count of the GPU solve."""
+    steps), else as many outer steps as fit, scaled per outer step (set-up
+    apart) to the outer-step count of the GPU solve."""
     import oracle
     cores = os.cpu_count() or 1
+    t_set = oracle_setup_s(p, alpha, omega, eps)
     t2, i2 = oracle_steps(p, alpha, omega, eps, 2)
-    per = t2 / max(1, i2["outer_iters"])
+    per = max(t2 - t_set, 1e-9) / max(1, i2["outer_iters"])
     want = gpu_outer or 1000
     if per * want <= budget_s:
         dt, info = oracle_steps(p, alpha, omega, eps, 100000)
@@ -780,17 +789,21 @@ def cpu_baseline(p, alpha, omega, eps, budget_s, gpu_outer=None):
     dt, info = oracle_steps(p, alpha, omega, eps, m)
     k = max(1, info["outer_iters"])
     scale = gpu_outer or k
-    return {"value": dt / k * scale, "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": f"{k} outer steps of FP64-inner GADI-IR on {p.name} in {dt:.2f} s, alpha {alpha:.4g}, "
-                      f"omega {omega:.4g}, scaled per outer step to the GPU solve's {scale} outer steps"}
+    return {"value": t_set + (dt - t_set) / k * scale, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"{k} outer steps of FP64-inner GADI-IR on {p.name} in {dt:.2f} s (set-up and first "
+                      f"residual {t_set:.2f} s), alpha {alpha:.4g}, omega {omega:.4g}, scaled per outer step "
+                      f"to the GPU solve's {scale} outer steps"}
 
 
 def run_reference(args, base, cfg):
     """The oracle as the reference arm: one full solve first (untimed: its
-    outer-step count), then K timed steps, each a bounded sample of the first
-    outer steps, scaled per outer step to the full solve's count. (alpha,
-    omega) come from the same predictor as the GPU arm's (trained on the GPU
-    in the set-up; the fixed pair without a GPU)."""
+    outer-step count and time), the set-up time of a call, and one untimed
+    sample of the first outer steps (about 3 s); then K timed steps, each
+    the same bounded sample, scaled to a full solve by the ratio of the full
+    solve's steps to the calibration sample's (set-up apart), so that the
+    early steps' different cost does not bias the estimate. (alpha, omega)
+    come from the same predictor as the GPU arm's (trained on the GPU in the
+    set-up; the fixed pair without a GPU)."""
     from paper_2501_04229_gb300 import problems as P
     names = [args.workload]
     try:
@@ -808,19 +821,23 @@ def run_reference(args, base, cfg):
     alpha, omega, source = params[args.workload]
     p = P.workload(args.workload)
     t_full, i_full = oracle_steps(p, alpha, omega, args.eps, 100000)
+    t_set = oracle_setup_s(p, alpha, omega, args.eps)
     full_outer = max(1, i_full["outer_iters"])
-    per_full = t_full / full_outer
-    sample_outer = max(2, min(full_outer, int(math.ceil(0.4 / max(per_full, 1e-6)))))
+    per_full = max(t_full - t_set, 1e-6) / full_outer
+    sample_outer = max(2, min(full_outer, int(math.ceil(3.0 / per_full))))
+    t_cal, _ = oracle_steps(p, alpha, omega, args.eps, sample_outer)
+    scale = (t_full - t_set) / max(t_cal - t_set, 1e-9)
     times = []
     for i in range(args.warmup + args.steps):
         dt, info = oracle_steps(p, alpha, omega, args.eps, sample_outer)
         if i >= args.warmup:
-            times.append(dt / max(1, info["outer_iters"]) * full_outer)
+            times.append(t_set + (dt - t_set) * scale)
     v = statistics.median(times)
     cb = {"value": v, "unit": "s", "cores": os.cpu_count() or 1, "kind": "oracle",
           "sample": f"each step: the first {sample_outer} outer steps of FP64-inner GADI-IR on {p.name}, "
-                    f"scaled per outer step to the {full_outer} outer steps of one full oracle solve "
-                    f"({t_full:.2f} s, status {i_full['status']}, eta {i_full['eta_inf']:.3g})",
+                    f"scaled (set-up and first residual, {t_set:.2f} s, apart) by {scale:.2f}, the ratio of "
+                    f"one full oracle solve ({full_outer} outer steps, {t_full:.2f} s, status "
+                    f"{i_full['status']}, eta {i_full['eta_inf']:.3g}) to an untimed sample ({t_cal:.2f} s)",
           "full_solve_s": t_full}
     cb.update(host_info())
     line = dict(base, impl="reference", value=v, ms_per_step=v * 1e3, dtype="f64", config=cfg,
