@@ -25,6 +25,12 @@
 // pass. CGNR (CG on S'^T S') needs two exchanges per iteration; its
 // search-direction and residual updates are fused into the products the
 // same way.
+//
+// A pass visits its rows in items of R consecutive rows of an x-line, taken
+// grid-stride; with the ZMarchOp family (3D constant-coefficient stencil,
+// 8-row items) the R, D, C0 and CGNR-A passes instead walk z-columns of
+// items (zmarch_items below), which forms the same rows from the same
+// terms in the same order.
 #pragma once
 
 #include <type_traits>
